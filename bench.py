@@ -1,0 +1,325 @@
+#!/usr/bin/env python3
+"""Benchmark of the SFA matcher: text GB/s on one GB300, bit-exact.
+
+Default workload (the single-automaton path): Aho-Corasick automaton of 16
+seeded literals (lengths 4..12, base64 alphabet, 127 states) over 1 GiB of
+Zipf(1.1) text with one planted literal per 64 KiB.  A step is one full match
+of the resident text (all chunks from f_I, the composition scan, the count
+pass) -- one launch.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl reference]
+
+Prints one JSON line.  Under torchrun (N > 1) every rank matches its own
+replica of the workload (weak scaling, no collective on the data path);
+rank 0 prints the aggregate.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads as W  # noqa: E402
+
+METRIC = "text GB/s per GB300 (and % of HBM peak), bit-exact"
+PEAK_FALLBACK_GBS = 6800.0
+KERNEL_SRC = os.path.join(ROOT, "paper_1405_0562_gb300", "csrc", "sfa_device.cuh")
+
+
+def kernel_hash() -> str:
+    with open(KERNEL_SRC, "rb") as fh:
+        return hashlib.sha256(fh.read()).hexdigest()[:16]
+
+
+def hbm_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except Exception:
+        return PEAK_FALLBACK_GBS, "fallback"
+
+
+def profiled_traffic(workload: str):
+    """DRAM bytes per launch of the match kernel from the committed ncu
+    summary, if it was taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", f"sfa_match_kernel_{workload}.txt")
+    try:
+        fields = {}
+        with open(path) as fh:
+            for line in fh:
+                if ":" in line:
+                    k, v = line.split(":", 1)
+                    fields[k.strip()] = v.strip()
+        if fields.get("kernel_source_sha256_16") != kernel_hash():
+            return None
+        return float(fields["dram_bytes_per_launch_full_size"])
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 100 ms."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            if self.thread:
+                self.thread.join(timeout=2)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(n_gpus: int):
+    if n_gpus <= 1 or "RANK" not in os.environ:
+        return 0, 1, 0
+    import torch
+    import torch.distributed as dist
+    rank, world = int(os.environ["RANK"]), int(os.environ["WORLD_SIZE"])
+    local = int(os.environ.get("LOCAL_RANK", rank))
+    torch.cuda.set_device(local)
+    dist.init_process_group("nccl")
+    return rank, world, local
+
+
+def barrier_max(value: float, world: int) -> float:
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ---------------------------------------------------------------------------
+# workloads
+# ---------------------------------------------------------------------------
+
+def make_workload(name: str):
+    if name == "plain_large":
+        d, t = W.workload_large()
+        return d, t, {"workload": "plain_large: Aho-Corasick DFA of 16 literals (len 4-12, base64 alphabet), "
+                                  "1 GiB Zipf(1.1) text, 1 plant per 64 KiB",
+                      "text_bytes": int(t.size), "dfa_states": d.nq, "seed": W.SEED_LARGE}
+    if name == "plain_small":
+        d, t = W.workload_single()
+        return d, t, {"workload": "plain_small: KMP DFA of one 6-byte literal over a-z (7 states), "
+                                  "1 MiB uniform a-z text, 64 plants",
+                      "text_bytes": int(t.size), "dfa_states": d.nq, "seed": W.SEED_SINGLE}
+    raise SystemExit(f"unknown workload {name}")
+
+
+def run_reference(args, rank: int, world: int):
+    """The oracle (sequential Alg. 2 in C, one host core) on a bounded sample
+    of the same workload per step."""
+    import oracle
+    if rank != 0:
+        return
+    d, t, cfg = make_workload(args.workload)
+    sample = min(t.size, 64 << 20)
+    for _ in range(max(args.warmup, 0)):
+        oracle.dfa_run(d.delta, d.q0, d.accept, t[:sample])
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.dfa_run(d.delta, d.q0, d.accept, t[:sample])
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = sample * args.steps / total / 1e9
+    desc = f"first {sample >> 20} MiB of the {t.size >> 20} MiB text per step"
+    line = {"metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic", "config": cfg,
+            "impl": "reference",
+            "cpu_baseline": {"value": value, "unit": "GB/s", "cores": 1, "kind": "oracle", "sample": desc},
+            "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(d, t, budget_s: float = 12.0):
+    """The oracle as it stands (Alg. 2 in C, one core) over the whole text,
+    repeated while it stays inside the budget."""
+    import oracle
+    reps, elapsed = 0, 0.0
+    while reps < 1 or (elapsed < budget_s and reps < 8):
+        t0 = time.perf_counter()
+        res = oracle.dfa_run(d.delta, d.q0, d.accept, t)
+        elapsed += time.perf_counter() - t0
+        reps += 1
+    return {"value": t.size * reps / elapsed / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "sample": f"whole {t.size >> 20} MiB text x {reps}"}, res
+
+
+def run_gpu(args, rank: int, world: int, local: int):
+    import torch
+
+    import paper_1405_0562_gb300 as sfa
+
+    torch.cuda.set_device(local)
+    d, t, cfg = make_workload(args.workload)
+    a = sfa.Automaton.from_dfa(d)
+    info = a.info()
+    cfg.update({"sfa_states": info["n_sfa_states"], "byte_classes": info["ncls"],
+                "l2": "inputs larger than L2" if t.size > (126 << 20) else "L2 flushed between steps"})
+    stream = torch.cuda.Stream()
+    text = torch.from_numpy(t).to(f"cuda:{local}")
+    out = sfa.empty_results(1, text.device)
+    flush = None if t.size > (126 << 20) else torch.empty(256 << 20, dtype=torch.uint8, device=text.device)
+    launch = {}
+
+    # correctness of what is timed (the oracle, when it is allowed to run)
+    with torch.cuda.stream(stream):
+        a.match(text, out, stream=stream, **launch)
+    stream.synchronize()
+    got = sfa.decode(out)[0]
+
+    for _ in range(args.warmup):
+        a.match(text, out, stream=stream, **launch)
+    stream.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier(world)
+    torch.cuda.synchronize()
+    n_before = sfa.kernel_launch_count()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for i in range(args.steps):
+        if flush is not None:
+            flush.fill_(i & 0xFF)
+        evs[i][0].record(stream)
+        a.match(text, out, stream=stream, **launch)
+        evs[i][1].record(stream)
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    launches = sfa.kernel_launch_count() - n_before
+    clk = clocks.stop()
+    total_ms = t_start.elapsed_time(t_end)
+    kern_ms = [s.elapsed_time(e) for s, e in evs]
+    total_ms = barrier_max(total_ms, world)
+    step_ms = total_ms / args.steps
+    if flush is not None:
+        step_ms = statistics.mean(kern_ms)   # flush writes are outside the per-step events
+    value = t.size * world / (step_ms * 1e-3) / 1e9
+
+    # end to end through the host-buffer entry point (copies inside)
+    pinned = torch.from_numpy(t).pin_memory()
+    e2e_steps = max(1, min(args.steps, 5))
+    a.match_host(pinned, stream=stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        res_h = a.match_host(pinned, stream=stream)
+    e2e_s = barrier_max((time.perf_counter() - t0) / e2e_steps, world)
+    assert res_h == got, (res_h, got)
+
+    peak, peak_kind = hbm_peak()
+    kern_avg = statistics.mean(kern_ms)
+    achieved = t.size / (kern_avg * 1e-3) / 1e9
+    traffic = profiled_traffic(args.workload)
+    line = {"metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u8", "data": "synthetic", "config": cfg,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "peak_kind": peak_kind, "kernel": "sfa_match_kernel",
+                         "algorithmic_bytes_per_launch": int(t.size)},
+            "e2e": {"value": t.size * world / e2e_s / 1e9, "unit": "GB/s", "h2d_bytes_per_step": int(t.size),
+                    "d2h_bytes_per_step": 16},
+            "gpu_launches": int(launches), "clocks": clk}
+    if rank == 0 and not args.no_cpu_baseline:
+        base, res = cpu_baseline(d, t)
+        line["cpu_baseline"] = base
+        line["bit_exact_vs_oracle"] = (got == (res[0], res[1], 0, res[2]))
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=4000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--workload", default="plain_large", choices=["plain_large", "plain_small"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    rank, world, local = dist_setup(args.gpus)
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_gpu(args, rank, world, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,252 @@
+/*
+ * sfa.h -- C ABI of the GB300 (sm_103a) simultaneous-finite-automaton matcher.
+ *
+ * The library runs the data-parallel computation of a D-SFA (Sin'ya,
+ * Matsuzaki, Sassa, "Simultaneous Finite Automata: An Efficient Data-Parallel
+ * Model for Regular Expression Matching", ICPP 2013) on one GPU:
+ *
+ *   - sfa_compile    builds the D-SFA of a DFA on the host (Alg. 4, with the
+ *                    DFA simplification of Sect. V-A) and uploads its tables;
+ *   - sfa_match*     split a text into chunks, run the SFA on every chunk from
+ *                    the identity state f_I (Alg. 5), combine the per-chunk
+ *                    mappings by reverse composition (Lemma 1, Theorem 3) and
+ *                    count the prefixes that end in a final state.
+ *
+ * Semantics of every match call, for a DFA (Q, Sigma, delta, {q0}, F) and a
+ * text w = w_1 .. w_n (Sect. II-B, Alg. 2):
+ *   final_state  = delta^(q0, w)            (q0 when n = 0)
+ *   accept_final = 1 iff final_state is in F
+ *   count        = #{ i in 1..n : delta^(q0, w_1..w_i) in F }
+ * (the empty prefix is not counted; overlapping occurrences all count).
+ * All results are integers and exact.
+ *
+ * Conventions
+ *   - State numbers in and out of the library are the caller's (0..nq-1).
+ *   - Pointers named d_* are device pointers of the current device; h_* and
+ *     unprefixed array arguments are host pointers.
+ *   - Match calls only enqueue work on `stream` and return; results are valid
+ *     once the stream has reached that point.  Inputs must stay alive and
+ *     unmodified until then.  Exception: sfa_match_host synchronises.
+ *   - Every function returns SFA_OK (0) or a negative SFA_ERR_* code and
+ *     never throws; sfa_strerror gives a message.
+ *   - A handle's scratch memory is shared by its match calls: calls on one
+ *     handle must not overlap on the GPU (use one stream per handle, or one
+ *     handle per stream).
+ */
+#ifndef SFA_H
+#define SFA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* The CUDA runtime's cudaStream_t (NULL = the legacy default stream). */
+typedef struct CUstream_st *sfa_stream_t;
+
+typedef struct sfa_handle *sfa_handle_t;
+typedef struct sfa_batch *sfa_batch_t;
+
+/* ---- error codes ------------------------------------------------------- */
+#define SFA_OK               0
+#define SFA_ERR_INVALID     -1  /* bad argument: DFA out of range, NULL pointer, size */
+#define SFA_ERR_UNSUPPORTED -2  /* valid but outside this build's limits (e.g. nq > 256) */
+#define SFA_ERR_OOM         -3  /* host or device allocation failed */
+#define SFA_ERR_CUDA        -4  /* a CUDA runtime call failed */
+#define SFA_ERR_TIMEOUT     -5  /* a device-side bounded wait gave up (see sfa_result.status) */
+#define SFA_ERR_NO_DEVICE   -6  /* no CUDA device is usable */
+#define SFA_ERR_HOST_ONLY   -7  /* the handle was compiled with SFA_COMPILE_HOST_ONLY */
+
+/* ---- result of one text (16 bytes, written to device memory) ----------- */
+typedef struct {
+    uint32_t final_state;   /* delta^(q0, w), caller's numbering */
+    uint8_t accept_final;   /* 1 iff final_state is final */
+    uint8_t status;         /* 0 = valid; SFA_STATUS_TIMEOUT = a device-side
+                               wait gave up and the other fields are invalid */
+    uint16_t reserved;
+    uint64_t count;         /* accepting prefixes, see above */
+} sfa_result;
+
+#define SFA_STATUS_OK      0
+#define SFA_STATUS_TIMEOUT 1
+
+/* ---- compile ------------------------------------------------------------ */
+#define SFA_MODE_AUTO 0     /* D-SFA if it stays within cap_states, else simulation */
+#define SFA_MODE_SFA  1     /* always the D-SFA (fails with UNSUPPORTED past the cap) */
+#define SFA_MODE_SIM  2     /* always the simulation path of Alg. 3 */
+
+#define SFA_COMPILE_HOST_ONLY 1u  /* build the tables on the host only; no device
+                                     memory, match calls fail with SFA_ERR_HOST_ONLY */
+
+typedef struct {
+    uint32_t cap_states;    /* max non-constant D-SFA states; 0 = 65536 */
+    int32_t force_mode;     /* SFA_MODE_* */
+    uint32_t flags;         /* SFA_COMPILE_* */
+    uint32_t reserved;
+} sfa_compile_opts;
+
+/*
+ * sfa_compile -- Alg. 4 (correspondence construction), Sect. V-A.
+ *   delta   host, int32[nq * 256], row-major: delta[q*256 + b] is the state
+ *           after reading byte b in state q; every entry in [0, nq)
+ *   nq      1..256 states
+ *   q0      initial state, [0, nq)
+ *   accept  host, uint8[nq]: nonzero = final state
+ *   opts    NULL for defaults
+ *   out     receives the handle (owns host and device tables)
+ * Synchronous.  Device tables go to the current device.  The D-SFA is built
+ * over the states reachable from q0 and over byte classes (bytes whose
+ * columns of delta are equal); when it has more than cap_states
+ * non-constant mappings the handle uses the simulation path (Alg. 3), which
+ * is not an error.  Errors: INVALID (range), UNSUPPORTED (nq > 256, or a
+ * simulation handle with more than 64 reachable states), OOM, CUDA,
+ * NO_DEVICE.
+ */
+int sfa_compile(const int32_t *delta, int32_t nq, int32_t q0, const uint8_t *accept,
+                const sfa_compile_opts *opts, sfa_handle_t *out);
+
+/* sfa_destroy -- frees a handle (NULL is fine).  The caller guarantees that
+ * no work using it is in flight. */
+void sfa_destroy(sfa_handle_t h);
+
+/* ---- information -------------------------------------------------------- */
+typedef struct {
+    uint32_t mode;            /* SFA_MODE_SFA or SFA_MODE_SIM */
+    uint32_t nq;              /* states given to sfa_compile */
+    uint32_t n_reachable;     /* states reachable from q0 (the ones kept) */
+    uint32_t n_accepting;     /* reachable final states */
+    uint32_t ncls;            /* byte classes */
+    uint32_t on_device;       /* 1 if device tables exist */
+    uint64_t n_sfa_states;    /* |Q_s| (reachable from f_I); 0 in SIM mode */
+    uint64_t n_nonconst;      /* of which non-constant mappings */
+    uint64_t table_bytes;     /* device bytes of all tables */
+    double compile_seconds;   /* host construction time */
+} sfa_info_t;
+
+/* sfa_info -- fills *out.  Thm. 2 bounds n_sfa_states by n_reachable^n_reachable. */
+int sfa_info(sfa_handle_t h, sfa_info_t *out);
+
+/* sfa_export -- copies one host table of the handle, for inspection and tests.
+ *   which: SFA_TABLE_CLASS  uint8[256]            class of each byte
+ *          SFA_TABLE_DFA    uint8[nr * 256]       renumbered DFA, row = state
+ *          SFA_TABLE_NC     uint32[n_nc * ncls]   non-constant D-SFA rows:
+ *                           next id in bits 0..29, class of next in 30..31
+ *                           (0 no state final, 1 all final, 2 mixed)
+ *          SFA_TABLE_MAPS   uint8[n_nc * nr]      mapping of each non-constant state
+ *          SFA_TABLE_ORIG   int32[nr]             caller's id of each kept state
+ *   Kept states are renumbered so that the final ones come last; D-SFA id
+ *   c < nr is the constant mapping onto state c, id nr + k the k-th
+ *   non-constant mapping in discovery order (k = 0 is f_I when nr > 1).
+ *   Writes min(bytes, table size); returns the table size in *size_out.
+ */
+#define SFA_TABLE_CLASS 0
+#define SFA_TABLE_DFA   1
+#define SFA_TABLE_NC    2
+#define SFA_TABLE_MAPS  3
+#define SFA_TABLE_ORIG  4
+int sfa_export(sfa_handle_t h, int32_t which, void *dst, size_t bytes, size_t *size_out);
+
+/* sfa_strerror -- static message for an SFA_* code. */
+const char *sfa_strerror(int code);
+
+/* ---- launch shape (all fields optional: 0 = automatic) ------------------ */
+#define SFA_DEBUG_SKIP_PUBLISH 1u  /* test knob: tile 1 never publishes its look-back
+                                      descriptor, so its successor's bounded wait runs out */
+
+typedef struct {
+    uint32_t chunk_bytes;     /* bytes per chunk (any value >= 1; 0 = automatic) */
+    uint32_t block_threads;   /* 128, 256 or 512 (0 = automatic) */
+    uint32_t chains;          /* chunks per thread: 1, 2 or 4 (0 = automatic) */
+    uint32_t max_ctas;        /* cap on resident CTAs (0 = all that fit) */
+    uint32_t forced_chunks;   /* >0: split the text into exactly this many chunks of
+                                 equal length (+-1 byte) instead of chunk_bytes */
+    uint32_t timeout_us;      /* bound on each device-side wait (0 = 2 s) */
+    uint32_t debug_flags;     /* SFA_DEBUG_* */
+    uint32_t reserved;
+} sfa_launch_opts;
+
+/* ---- matching ------------------------------------------------------------ */
+
+/*
+ * sfa_match -- Alg. 5 on the GPU for one device-resident text.
+ *   d_text  device, n bytes (any alignment); may be NULL when n = 0
+ *   n       text length, up to 2^40
+ *   d_out   device, one sfa_result
+ * The text is split into chunks; every chunk is run from f_I; the chunk
+ * mappings are combined by warp, block and grid (decoupled look-back) scans
+ * of reverse compositions (Lemma 1, Theorem 3); a second pass over each
+ * chunk's prefix before its last "mixed" position counts final states.
+ * May grow the handle's scratch (cudaMalloc) when n exceeds all previous calls.
+ */
+int sfa_match(sfa_handle_t h, const uint8_t *d_text, uint64_t n, sfa_result *d_out,
+              sfa_stream_t stream);
+
+/* sfa_match_ex -- sfa_match with an explicit launch shape (opts may be NULL). */
+int sfa_match_ex(sfa_handle_t h, const uint8_t *d_text, uint64_t n, sfa_result *d_out,
+                 sfa_stream_t stream, const sfa_launch_opts *opts);
+
+/*
+ * sfa_match_continue -- streaming form of Lemma 1: *d_inout holds the result
+ * for a text u (as written by a previous match call on this handle); on
+ * completion it holds the result for u w, where w = d_text[0..n).  So a long
+ * text can be matched piece by piece with identical results.
+ */
+int sfa_match_continue(sfa_handle_t h, const uint8_t *d_text, uint64_t n, sfa_result *d_inout,
+                       sfa_stream_t stream, const sfa_launch_opts *opts);
+
+/*
+ * sfa_match_host -- end-to-end form: host text in, host result out.
+ *   h_text  host, n bytes (pinned memory gives full copy bandwidth)
+ *   h_out   host, one sfa_result
+ * Copies the text to the device in pieces on a second stream, overlapping
+ * each copy with the matching of the previous piece (sfa_match_continue),
+ * and synchronises before returning.  Uses handle-owned staging buffers.
+ */
+int sfa_match_host(sfa_handle_t h, const uint8_t *h_text, uint64_t n, sfa_result *h_out,
+                   sfa_stream_t stream, const sfa_launch_opts *opts);
+
+/* ---- batches ------------------------------------------------------------- */
+
+/*
+ * sfa_batch_create -- plans one persistent launch over k texts, each matched
+ * with its own automaton (Theorem 3 applied per text: every text gets its own
+ * look-back chain of tiles).
+ *   hs       host, k handles (all compiled on the current device, SFA mode;
+ *            simulation-mode handles are matched by per-text launches)
+ *   d_texts  host array of k device pointers
+ *   lens     host, k lengths
+ *   opts     launch shape (NULL = automatic)
+ * The work list (texts sorted by automaton, tiles in text order) and the
+ * scratch are allocated and uploaded here, synchronously; launches of the
+ * plan allocate nothing and can be captured in a CUDA graph.
+ */
+int sfa_batch_create(const sfa_handle_t *hs, const uint8_t *const *d_texts, const uint64_t *lens,
+                     int32_t k, const sfa_launch_opts *opts, sfa_batch_t *out);
+
+/* sfa_batch_launch -- enqueue the planned work; d_out: device, k results in
+ * the order of the texts given to sfa_batch_create.  Launches of one plan
+ * must not overlap on the GPU. */
+int sfa_batch_launch(sfa_batch_t b, sfa_result *d_out, sfa_stream_t stream);
+
+/* sfa_batch_graph_launch -- as sfa_batch_launch, but through a CUDA graph
+ * captured on the first call for this (d_out) and replayed afterwards. */
+int sfa_batch_graph_launch(sfa_batch_t b, sfa_result *d_out, sfa_stream_t stream);
+
+/* sfa_batch_destroy -- frees a plan (NULL is fine); no launch may be in flight. */
+void sfa_batch_destroy(sfa_batch_t b);
+
+/* sfa_match_batch -- create + launch + destroy (destroy after the stream
+ * synchronises).  For repeated batches keep a plan instead. */
+int sfa_match_batch(const sfa_handle_t *hs, const uint8_t *const *d_texts, const uint64_t *lens,
+                    int32_t k, sfa_result *d_out, sfa_stream_t stream);
+
+/* ---- launch statistics (for benchmarks) --------------------------------- */
+/* Number of kernels the library enqueued since load (all entry points). */
+uint64_t sfa_kernel_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SFA_H */

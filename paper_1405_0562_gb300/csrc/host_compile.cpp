@@ -1,0 +1,202 @@
+// D-SFA construction on the host: Alg. 4 (correspondence construction) with
+// the DFA simplification of Sect. V-A, f_next(q) = delta(f(q), sigma).
+//
+// Steps (all exact, none changes a match result):
+//  1. validate the DFA (Sect. II-B: total table, one initial state);
+//  2. keep the states reachable from q0 -- every state a chunk can be
+//     entered in is one of them -- and renumber them so that the final
+//     states are the ids [first_accept, nr);
+//  3. merge bytes whose columns of delta are equal into classes (the
+//     alphabet Sigma of Alg. 4 becomes the set of classes);
+//  4. breadth-first correspondence construction from f_I over the classes,
+//     with a FIFO worklist.  Constant mappings q -> c are not stored as
+//     rows of their own: their SFA transition is c . delta^sigma, the
+//     constant onto delta(c, sigma), i.e. the DFA row of c.  They get the
+//     ids 0..nr-1 (the id is the constant's value) and the DFA table serves
+//     as their part of the transition table.  Non-constant mappings get ids
+//     nr, nr+1, ... in discovery order;
+//  5. past `cap` non-constant mappings the handle uses the simulation path
+//     of Alg. 3 instead (Theorem 2 bounds the D-SFA only by nr^nr).
+#include "host_compile.h"
+
+#include <chrono>
+#include <cstring>
+#include <string>
+#include <unordered_map>
+
+#include "sfa.h"
+
+namespace sfa_impl {
+
+namespace {
+
+struct VecHash {
+    size_t operator()(const std::string &s) const noexcept {
+        // 64-bit FNV-1a over the mapping bytes
+        uint64_t h = 0xcbf29ce484222325ull;
+        for (unsigned char c : s) {
+            h ^= c;
+            h *= 0x100000001b3ull;
+        }
+        return (size_t)h;
+    }
+};
+
+uint32_t acc_class(const uint8_t *f, int nr, int first_accept) {
+    bool any = false, all = true;
+    for (int q = 0; q < nr; ++q) {
+        bool fin = f[q] >= first_accept;
+        any |= fin;
+        all &= fin;
+    }
+    return all ? ACC_ALL : (any ? ACC_MIXED : ACC_NONE);
+}
+
+}  // namespace
+
+int build_tables(const int32_t *delta, int32_t nq, int32_t q0, const uint8_t *accept,
+                 uint32_t cap, int32_t force_mode, HostTables &T) {
+    auto t0 = std::chrono::steady_clock::now();
+    if (!delta || !accept) return SFA_ERR_INVALID;
+    if (nq < 1) return SFA_ERR_INVALID;
+    if (nq > 256) return SFA_ERR_UNSUPPORTED;
+    if (q0 < 0 || q0 >= nq) return SFA_ERR_INVALID;
+    for (int64_t i = 0; i < (int64_t)nq * 256; ++i)
+        if (delta[i] < 0 || delta[i] >= nq) return SFA_ERR_INVALID;
+    if (force_mode < SFA_MODE_AUTO || force_mode > SFA_MODE_SIM) return SFA_ERR_INVALID;
+    if (cap == 0) cap = DEFAULT_CAP;
+    if (cap > NC_ID_MASK - 256) cap = NC_ID_MASK - 256;
+
+    // 2. reachable states, breadth first from q0, then final states last
+    std::vector<int32_t> order;
+    std::vector<char> seen(nq, 0);
+    order.push_back(q0);
+    seen[q0] = 1;
+    for (size_t i = 0; i < order.size(); ++i)
+        for (int b = 0; b < 256; ++b) {
+            int32_t t = delta[(int64_t)order[i] * 256 + b];
+            if (!seen[t]) {
+                seen[t] = 1;
+                order.push_back(t);
+            }
+        }
+    T.nq_in = nq;
+    T.nr = (int32_t)order.size();
+    T.orig_of.clear();
+    for (int32_t s : order)
+        if (!accept[s]) T.orig_of.push_back(s);
+    T.first_accept = (int32_t)T.orig_of.size();
+    for (int32_t s : order)
+        if (accept[s]) T.orig_of.push_back(s);
+    T.kept_of.assign(nq, -1);
+    for (int32_t i = 0; i < T.nr; ++i) T.kept_of[T.orig_of[i]] = i;
+    T.q0 = T.kept_of[q0];
+    const int nr = T.nr;
+    T.dfa.assign((size_t)nr * 256, 0);
+    for (int i = 0; i < nr; ++i)
+        for (int b = 0; b < 256; ++b)
+            T.dfa[(size_t)i * 256 + b] = (uint8_t)T.kept_of[delta[(int64_t)T.orig_of[i] * 256 + b]];
+
+    // 3. byte classes: equal columns of the kept table, numbered by first byte
+    {
+        std::unordered_map<std::string, int, VecHash> cols;
+        std::string col(nr, '\0');
+        T.ncls = 0;
+        for (int b = 0; b < 256; ++b) {
+            for (int i = 0; i < nr; ++i) col[i] = (char)T.dfa[(size_t)i * 256 + b];
+            auto it = cols.find(col);
+            if (it == cols.end()) it = cols.emplace(col, T.ncls++).first;
+            T.cls[b] = (uint8_t)it->second;
+        }
+    }
+    const int ncls = T.ncls;
+    std::vector<uint8_t> rep(ncls);  // a representative byte of each class
+    for (int b = 255; b >= 0; --b) rep[T.cls[b]] = (uint8_t)b;
+
+    T.ident = nr > 1 ? (uint32_t)nr : 0u;
+    T.n_nc = 0;
+    T.nc.clear();
+    T.maps.clear();
+    T.n_const = 0;
+    T.mode = SFA_MODE_SFA;
+
+    bool sim = force_mode == SFA_MODE_SIM;
+    if (!sim && nr > 1) {
+        // 4. correspondence construction over the non-constant mappings
+        std::unordered_map<std::string, uint32_t, VecHash> ids;
+        ids.reserve(1024);
+        std::string f(nr, '\0'), g(nr, '\0');
+        for (int q = 0; q < nr; ++q) f[q] = (char)q;
+        T.maps.insert(T.maps.end(), f.begin(), f.end());
+        ids.emplace(f, 0);
+        T.n_nc = 1;
+        for (uint64_t head = 0; head < T.n_nc && !sim; ++head) {
+            for (int c = 0; c < ncls; ++c) {
+                const uint8_t *fm = T.maps.data() + head * nr;
+                const uint8_t *row_b = T.dfa.data() + rep[c];
+                bool constant = true;
+                for (int q = 0; q < nr; ++q) {
+                    g[q] = (char)row_b[(size_t)fm[q] * 256];
+                    constant &= g[q] == g[0];
+                }
+                uint32_t id;
+                if (constant) {
+                    id = (uint8_t)g[0];
+                } else {
+                    auto it = ids.find(g);
+                    if (it == ids.end()) {
+                        if (T.n_nc >= cap) {
+                            sim = true;
+                            break;
+                        }
+                        it = ids.emplace(g, (uint32_t)T.n_nc).first;
+                        T.maps.insert(T.maps.end(), g.begin(), g.end());
+                        ++T.n_nc;
+                    }
+                    id = (uint32_t)nr + it->second;
+                }
+                T.nc.push_back(id);  // class bits added below
+            }
+        }
+        if (sim && force_mode == SFA_MODE_SFA) return SFA_ERR_UNSUPPORTED;
+    }
+    if (sim) {
+        if (nr > SIM_MAX_STATES) return SFA_ERR_UNSUPPORTED;
+        T.mode = SFA_MODE_SIM;
+        T.n_nc = 0;
+        T.nc.clear();
+        T.maps.clear();
+    } else {
+        // acceptance class of each target, packed into the entry
+        for (uint64_t i = 0; i < T.nc.size(); ++i) {
+            uint32_t id = T.nc[i];
+            uint32_t a = id < (uint32_t)nr ? ((int)id >= T.first_accept ? ACC_ALL : ACC_NONE)
+                                           : acc_class(T.maps.data() + (size_t)(id - nr) * nr, nr,
+                                                       T.first_accept);
+            T.nc[i] = id | (a << NC_ACC_SHIFT);
+        }
+        // constant mappings reachable from f_I: the targets of non-constant
+        // rows (or f_I itself when nr = 1), closed under the DFA rows
+        std::vector<char> reach(nr, 0);
+        std::vector<int> stack;
+        auto mark = [&](int c) {
+            if (!reach[c]) {
+                reach[c] = 1;
+                stack.push_back(c);
+            }
+        };
+        if (nr == 1) mark(0);
+        for (uint32_t e : T.nc)
+            if ((e & NC_ID_MASK) < (uint32_t)nr) mark((int)(e & NC_ID_MASK));
+        while (!stack.empty()) {
+            int c = stack.back();
+            stack.pop_back();
+            for (int k = 0; k < ncls; ++k) mark(T.dfa[(size_t)c * 256 + rep[k]]);
+        }
+        for (char r : reach) T.n_const += r ? 1 : 0;
+    }
+    T.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    return SFA_OK;
+}
+
+}  // namespace sfa_impl

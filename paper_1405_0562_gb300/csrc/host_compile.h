@@ -1,0 +1,41 @@
+// Host-side construction of the D-SFA tables (no CUDA in this unit).
+#pragma once
+
+#include <cstdint>
+#include <vector>
+
+namespace sfa_impl {
+
+// acceptance class of a mapping f over the kept states: whether f(q) is final
+// for no q, for every q, or for some q only ("mixed")
+enum AccClass : uint32_t { ACC_NONE = 0, ACC_ALL = 1, ACC_MIXED = 2 };
+
+constexpr uint32_t NC_ID_MASK = 0x3fffffffu;
+constexpr int NC_ACC_SHIFT = 30;
+constexpr uint32_t DEFAULT_CAP = 65536;
+constexpr int SIM_MAX_STATES = 64;
+
+struct HostTables {
+    int32_t nq_in = 0;             // states given by the caller
+    int32_t nr = 0;                // states reachable from q0 (kept)
+    int32_t q0 = 0;                // kept numbering
+    int32_t first_accept = 0;      // kept ids [first_accept, nr) are final
+    int32_t ncls = 0;              // byte classes
+    uint8_t cls[256] = {};         // class of each byte
+    std::vector<int32_t> orig_of;  // [nr]     caller id of a kept state
+    std::vector<int32_t> kept_of;  // [nq_in]  kept id of a caller state, -1 if unreachable
+    std::vector<uint8_t> dfa;      // [nr*256] kept DFA over bytes
+    int32_t mode = 0;              // SFA_MODE_SFA or SFA_MODE_SIM
+    uint32_t ident = 0;            // D-SFA id of f_I (nr when nr > 1, else 0)
+    uint64_t n_nc = 0;             // non-constant D-SFA states
+    std::vector<uint32_t> nc;      // [n_nc*ncls] next id | acc class of next << 30
+    std::vector<uint8_t> maps;     // [n_nc*nr]   f(q) of each non-constant state
+    uint64_t n_const = 0;          // constant mappings reachable from f_I
+    double seconds = 0.0;
+};
+
+// Returns SFA_OK or an SFA_ERR_* code (see sfa.h for the rules).
+int build_tables(const int32_t *delta, int32_t nq, int32_t q0, const uint8_t *accept,
+                 uint32_t cap, int32_t force_mode, HostTables &out);
+
+}  // namespace sfa_impl

@@ -1,0 +1,56 @@
+// D-SFA-mode instances of the persistent matching kernel (single text and
+// batch forms) for every supported launch shape.
+#include "launch.h"
+#include "sfa_device.cuh"
+
+namespace sfa_impl {
+
+using sfa_dev::sfa_match_kernel;
+
+#define SFA_K(T, C, B) reinterpret_cast<const void *>(&sfa_match_kernel<T, C, 0, B>)
+
+const void *kernel_for_sfa(int threads, int chains, bool batch) {
+    if (batch) {
+        if (threads == 128 && chains == 1) return SFA_K(128, 1, true);
+        if (threads == 128 && chains == 2) return SFA_K(128, 2, true);
+        if (threads == 128 && chains == 4) return SFA_K(128, 4, true);
+        if (threads == 256 && chains == 1) return SFA_K(256, 1, true);
+        if (threads == 256 && chains == 2) return SFA_K(256, 2, true);
+        if (threads == 256 && chains == 4) return SFA_K(256, 4, true);
+        if (threads == 512 && chains == 1) return SFA_K(512, 1, true);
+        if (threads == 512 && chains == 2) return SFA_K(512, 2, true);
+        return nullptr;
+    }
+    if (threads == 128 && chains == 1) return SFA_K(128, 1, false);
+    if (threads == 128 && chains == 2) return SFA_K(128, 2, false);
+    if (threads == 128 && chains == 4) return SFA_K(128, 4, false);
+    if (threads == 256 && chains == 1) return SFA_K(256, 1, false);
+    if (threads == 256 && chains == 2) return SFA_K(256, 2, false);
+    if (threads == 256 && chains == 4) return SFA_K(256, 4, false);
+    if (threads == 512 && chains == 1) return SFA_K(512, 1, false);
+    if (threads == 512 && chains == 2) return SFA_K(512, 2, false);
+    return nullptr;
+}
+
+size_t smem_bytes(int threads, int chains, uint32_t nr_max) {
+    using namespace sfa_dev;
+    switch (threads * 8 + chains) {
+        case 128 * 8 + 1: return SmemLayout<128, 1>::bytes(nr_max);
+        case 128 * 8 + 2: return SmemLayout<128, 2>::bytes(nr_max);
+        case 128 * 8 + 4: return SmemLayout<128, 4>::bytes(nr_max);
+        case 256 * 8 + 1: return SmemLayout<256, 1>::bytes(nr_max);
+        case 256 * 8 + 2: return SmemLayout<256, 2>::bytes(nr_max);
+        case 256 * 8 + 4: return SmemLayout<256, 4>::bytes(nr_max);
+        case 512 * 8 + 1: return SmemLayout<512, 1>::bytes(nr_max);
+        case 512 * 8 + 2: return SmemLayout<512, 2>::bytes(nr_max);
+        default: return 0;
+    }
+}
+
+const void *kernel_for(int threads, int chains, int simnq, bool batch) {
+    if (simnq == 0) return kernel_for_sfa(threads, chains, batch);
+    if (batch) return nullptr;
+    return kernel_for_sim(threads, chains, simnq);
+}
+
+}  // namespace sfa_impl

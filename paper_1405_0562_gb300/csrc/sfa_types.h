@@ -1,0 +1,109 @@
+// Data layouts shared by the host launcher and the kernels: table and text
+// descriptors, per-launch scratch, shared-memory layout of a CTA.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#ifdef __CUDACC__
+#define SFA_HD __host__ __device__
+#else
+#define SFA_HD
+#endif
+
+namespace sfa_dev {
+
+constexpr uint32_t NC_ID_MASK = 0x3fffffffu;
+constexpr uint32_t ACC_ALL = 1, ACC_MIXED = 2;
+
+// look-back descriptor: flag in bits 62..63, value (a kept DFA state) below
+constexpr uint64_t ST_AGG = 1ull << 62;
+constexpr uint64_t ST_PREFIX = 2ull << 62;
+
+struct Tables {
+    const uint8_t *dfa;        // [nr*256]     kept DFA, final states last
+    const uint8_t *cls;        // [256]        byte -> class
+    const uint32_t *nc;        // [n_nc*ncls]  non-constant SFA rows
+    const uint8_t *maps;       // [n_nc*nr]    mappings of non-constant states
+    const int32_t *orig_of;    // [nr]
+    const int32_t *kept_of;    // [nq_in]
+    uint32_t nr, ncls, first_accept, q0, ident, nq_in, mode, pad;
+};
+
+struct TextDesc {
+    const uint8_t *text;
+    uint64_t n;
+    uint64_t chunk;            // bytes per chunk when forced == 0
+    uint32_t forced;           // exact number of chunks, or 0
+    uint32_t ntiles;
+    uint32_t tile_base;        // first global tile of the text
+    uint32_t table;            // index into the table array (batches)
+    uint32_t out_index;
+    uint32_t carry;            // 1: continue from out[out_index] (Lemma 1)
+};
+
+struct TextState {             // zeroed before each launch
+    unsigned long long count;
+    uint32_t done;
+    uint32_t final_state;
+    uint32_t err;
+    uint32_t pad[3];
+};
+
+struct LaunchHeader {          // zeroed before each launch
+    uint32_t tile_ctr;
+    uint32_t err;
+    uint32_t pad[14];
+};
+
+struct Scratch {
+    LaunchHeader *hdr;
+    TextState *texts;
+    uint64_t *status;          // [total tiles]
+    uint8_t *agg;              // [total tiles * nr_max]   tile aggregates
+    uint8_t *chainvec;         // [total tiles * CPT * nr]  chunk vectors (simulation only)
+    uint32_t nr_max;
+    uint32_t timeout_us;
+    uint32_t debug;
+    uint32_t total_tiles;
+};
+
+SFA_HD inline uint64_t num_chunks(const TextDesc &d) {
+    if (d.forced) return d.forced;
+    uint64_t c = (d.n + d.chunk - 1) / d.chunk;
+    return c ? c : 1;
+}
+
+// ---------------------------------------------------------------------------
+// shared memory of one CTA
+// ---------------------------------------------------------------------------
+template <int THREADS, int CH>
+struct SmemLayout {
+    static constexpr int CPT = THREADS * CH;   // chunks per tile
+    static constexpr int NW = THREADS / 32;
+    static constexpr int G = CPT / 32;         // groups per tile
+    static_assert(G <= 32, "at most 1024 chunks per tile");
+    // offsets in bytes from the start of dynamic shared memory
+    static SFA_HD size_t dfa_off() { return 0; }
+    static SFA_HD size_t cls_off(uint32_t nr_max) { return (size_t)nr_max * 256; }
+    static SFA_HD size_t f_off(uint32_t nr_max) { return cls_off(nr_max) + 256; }
+    static SFA_HD size_t gval_off(uint32_t nr_max) { return f_off(nr_max) + CPT * 4; }
+    static SFA_HD size_t gpre_off(uint32_t nr_max) { return gval_off(nr_max) + 32 * 4; }
+    static SFA_HD size_t misc_off(uint32_t nr_max) { return gpre_off(nr_max) + 32 * 4; }
+    static SFA_HD size_t gvec_off(uint32_t nr_max) { return misc_off(nr_max) + 256; }
+    static SFA_HD size_t bytes(uint32_t nr_max) {
+        return (gvec_off(nr_max) + (size_t)G * nr_max + 15) & ~(size_t)15;
+    }
+};
+
+struct Misc {
+    uint32_t tile;          // global tile being processed
+    uint32_t gconst;        // bit g: group g is a constant mapping
+    uint32_t s_in;          // entering state of the tile
+    uint32_t incl;          // state after the tile
+    uint32_t pad[4];
+    unsigned long long wsum[16];
+};
+static_assert(sizeof(Misc) <= 256, "misc region");
+
+}  // namespace sfa_dev

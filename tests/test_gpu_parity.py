@@ -1,0 +1,311 @@
+"""GPU parity: every result of the CUDA path (through the C ABI) equals the
+CPU oracle's, bit for bit (all outputs are integers: final state, accept
+bit, uint64 count; tolerance 0)."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _device():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    import paper_1405_0562_gb300 as sfa
+    sfa.lib()
+    torch.cuda.set_device(0)
+    yield
+
+
+def sfa_mod():
+    import paper_1405_0562_gb300 as sfa
+    return sfa
+
+
+def gpu_match(a, text_np, **launch):
+    t = torch.from_numpy(np.ascontiguousarray(text_np, dtype=np.uint8)).cuda()
+    out = a.match(t, **launch)
+    torch.cuda.synchronize()
+    return sfa_mod().decode(out)[0]
+
+
+def expect(d, text_np):
+    f, acc, c = oracle.dfa_run(d.delta, d.q0, d.accept, text_np)
+    return (f, acc, 0, c)
+
+
+def text_for(d, n, seed):
+    rng = np.random.default_rng(seed)
+    alpha = np.frombuffer(d.alphabet, dtype=np.uint8)
+    t = alpha[rng.integers(0, len(alpha), n)]
+    if d.name.startswith(("r_", "even_odd")) and n > 0:
+        # mostly accepted text with rare errors, so counts are large; k is
+        # the length of the automaton's loop
+        k = d.nq - 3 if d.name.startswith("r_a") else d.nq - 1
+        base = []
+        for i in range(n):
+            pos = i % k
+            if d.name.startswith("even_odd"):
+                base.append(b"02468"[rng.integers(0, 5)] if pos % 2 == 0 else b"13579"[rng.integers(0, 5)])
+            else:
+                base.append(b"01234"[rng.integers(0, 5)] if pos < k // 2 else b"56789"[rng.integers(0, 5)])
+        t = np.array(base, dtype=np.uint8)
+        flips = rng.integers(0, n, max(1, n // 5000))
+        t[flips] = alpha[rng.integers(0, len(alpha), flips.size)]
+    return t
+
+
+AUTOMATA = {
+    "ab_star": W.dfa_ab_star,
+    "r3": lambda: W.dfa_rn(3),
+    "r5": lambda: W.dfa_rn(5),
+    "ra2": lambda: W.dfa_ra(2),
+    "even_odd5": lambda: W.dfa_even_odd(5),
+    "T4": lambda: W.dfa_full_transformation(4),
+    "kmp": lambda: W.dfa_kmp(b"abcaab"),
+    "ac": lambda: W.dfa_aho_corasick([b"he", b"she", b"his", b"hers"]),
+    "ac_set": lambda: W.literal_set_automaton(11),
+    "rand8": lambda: W.dfa_random(8, 4, seed=3),
+    "single": lambda: W.workload_single(1 << 12)[0],
+    "one_state": lambda: W.DFA(np.zeros((1, 256), np.int32), 0, np.ones(1, np.uint8), b"ab", name="one"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(AUTOMATA))
+@pytest.mark.parametrize("n", [0, 1, 15, 16, 17, 1000, 65536 + 13, 1 << 20])
+def test_default_shape(name, n):
+    d = AUTOMATA[name]()
+    a = sfa_mod().Automaton.from_dfa(d)
+    t = text_for(d, n, seed=n)
+    assert gpu_match(a, t) == expect(d, t)
+
+
+@pytest.mark.parametrize("name", ["ab_star", "r3", "ac", "rand8", "T4"])
+def test_forced_chunk_counts_1_to_64(name):
+    """Theorem 3: any division gives the same result (1..64 chunks)."""
+    d = AUTOMATA[name]()
+    a = sfa_mod().Automaton.from_dfa(d)
+    for n in (0, 5, 3001):
+        t = text_for(d, n, seed=7)
+        want = expect(d, t)
+        for p in range(1, 65):
+            assert gpu_match(a, t, forced_chunks=p) == want, (n, p)
+            assert gpu_match(a, t, forced_chunks=p, block_threads=128, chains=1) == want, (n, p)
+
+
+@pytest.mark.parametrize("threads,chains", [(128, 1), (128, 2), (128, 4), (256, 1), (256, 2), (256, 4),
+                                            (512, 1), (512, 2)])
+@pytest.mark.parametrize("chunk", [1, 7, 16, 100, 1024])
+def test_launch_shapes(threads, chains, chunk):
+    for name in ("ac_set", "r5", "even_odd5"):
+        d = AUTOMATA[name]()
+        a = sfa_mod().Automaton.from_dfa(d)
+        t = text_for(d, 200_003, seed=chunk)
+        assert gpu_match(a, t, block_threads=threads, chains=chains, chunk_bytes=chunk) == expect(d, t), name
+
+
+def test_many_tiles_with_max_ctas():
+    """Look-back over hundreds of tiles with few resident CTAs."""
+    for name in ("r5", "ac_set", "T4"):
+        d = AUTOMATA[name]()
+        a = sfa_mod().Automaton.from_dfa(d)
+        t = text_for(d, 300_000, seed=1)
+        for ctas in (1, 2, 7):
+            assert gpu_match(a, t, chunk_bytes=16, block_threads=128, chains=1, max_ctas=ctas) == expect(d, t)
+
+
+@pytest.mark.parametrize("offset", range(16))
+def test_unaligned_text(offset):
+    d = AUTOMATA["ac_set"]()
+    a = sfa_mod().Automaton.from_dfa(d)
+    base = text_for(d, 100_000, seed=2)
+    buf = torch.from_numpy(base).cuda()
+    for n in (0, 1, 17, 4095, 60_000):
+        view = buf[offset:offset + n]
+        out = a.match(view, chunk_bytes=48)
+        torch.cuda.synchronize()
+        assert sfa_mod().decode(out)[0] == expect(d, base[offset:offset + n])
+
+
+def test_literal_boundaries_inside_chunks():
+    """Plants straddling chunk and tile boundaries."""
+    lit = b"needle!"
+    d = W.dfa_kmp(lit)
+    a = sfa_mod().Automaton.from_dfa(d)
+    t = W.text_uniform(1 << 16, W.LOWER_ALPHABET, 5)
+    for chunk in (16, 64, 256):
+        for s in range(chunk - len(lit) + 1, chunk + 1):
+            t2 = t.copy()
+            for base in range(0, len(t2) - 2 * chunk, 7 * chunk):
+                t2[base + s:base + s + len(lit)] = np.frombuffer(lit, np.uint8)
+            assert gpu_match(a, t2, chunk_bytes=chunk, block_threads=128, chains=1) == expect(d, t2)
+
+
+# ---------------------------------------------------------------------------
+# simulation mode (Alg. 3 vectors)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("idx", range(3))
+def test_simulation_random_dfas(idx):
+    d = W.workload_sim_automata()[idx]
+    a = sfa_mod().Automaton.from_dfa(d)
+    assert a.info()["mode"] == sfa_mod().MODE_SIM
+    t = W.text_uniform((1 << 22) + 5, bytes(range(16)), 100 + idx)
+    assert gpu_match(a, t) == expect(d, t)
+    for chunk in (64, 1000, 8192):
+        assert gpu_match(a, t[:300_001], chunk_bytes=chunk) == expect(d, t[:300_001])
+
+
+@pytest.mark.parametrize("name", ["ab_star", "r3", "T4", "kmp", "rand8", "even_odd5", "one_state"])
+def test_forced_simulation_small(name):
+    """Forced simulation, including chunks that never converge (r3 and T4
+    contain permutations), exercises the chunk-vector scan."""
+    d = AUTOMATA[name]()
+    a = sfa_mod().Automaton.from_dfa(d, mode=sfa_mod().MODE_SIM)
+    assert a.info()["mode"] == sfa_mod().MODE_SIM
+    for n in (0, 1, 33, 5000, 100_003):
+        t = text_for(d, n, seed=n)
+        want = expect(d, t)
+        assert gpu_match(a, t) == want
+        assert gpu_match(a, t, chunk_bytes=16, block_threads=128, chains=1) == want
+        assert gpu_match(a, t, chunk_bytes=40, block_threads=128, chains=2) == want
+    t = text_for(d, 2000, seed=9)
+    for p in range(1, 65):
+        assert gpu_match(a, t, forced_chunks=p) == expect(d, t)
+
+
+# ---------------------------------------------------------------------------
+# streaming (Lemma 1), host path, batches, timeouts
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("name", ["ac_set", "r5", "rand8"])
+def test_match_continue_pieces(name):
+    d = AUTOMATA[name]()
+    a = sfa_mod().Automaton.from_dfa(d)
+    t = text_for(d, 500_000, seed=4)
+    tt = torch.from_numpy(t).cuda()
+    rng = np.random.default_rng(0)
+    cuts = np.sort(rng.integers(0, len(t), 9)).tolist()
+    bounds = [0] + cuts + [len(t)]
+    out = a.match(tt[:bounds[1]])
+    for i in range(1, len(bounds) - 1):
+        a.match_continue(tt[bounds[i]:bounds[i + 1]], out, chunk_bytes=64)
+    torch.cuda.synchronize()
+    assert sfa_mod().decode(out)[0] == expect(d, t)
+
+
+def test_match_host_pinned_and_pageable():
+    d, t = W.workload_large(150 << 20)   # several 64 MiB pieces
+    a = sfa_mod().Automaton.from_dfa(d)
+    want = expect(d, t)
+    assert a.match_host(t) == want
+    pinned = torch.from_numpy(t).pin_memory()
+    assert a.match_host(pinned) == want
+    assert a.match_host(t[:0]) == expect(d, t[:0])
+
+
+def test_batch_mixed_and_graph():
+    sfa = sfa_mod()
+    autos_d = W.workload_batch_automata(4) + [W.dfa_rn(3), W.workload_sim_automata()[0]]
+    autos = [sfa.Automaton.from_dfa(d) for d in autos_d]
+    rng = np.random.default_rng(3)
+    lens = [0, 1, 16, 255, 256, 4097, 100_000, 1 << 20, 3, 70_001, 2 << 20, 999]
+    texts, hs, ds = [], [], []
+    for i, n in enumerate(lens):
+        j = int(rng.integers(0, len(autos)))
+        d = autos_d[j]
+        texts.append(text_for(d, n, seed=i))
+        hs.append(autos[j])
+        ds.append(d)
+    tt = [torch.from_numpy(x).cuda() for x in texts]
+    want = [expect(d, x) for d, x in zip(ds, texts)]
+    out = sfa.match_batch(hs, tt)
+    torch.cuda.synchronize()
+    assert sfa.decode(out) == want
+    b = sfa.Batch(hs, tt)
+    for graph in (False, True, True):
+        out = torch.zeros(16 * len(lens), dtype=torch.uint8, device="cuda")
+        b.launch(out, graph=graph)
+        torch.cuda.synchronize()
+        assert sfa.decode(out) == want
+    # each result alone equals the result in the mix
+    for i in range(len(lens)):
+        assert gpu_match(hs[i], texts[i]) == want[i]
+
+
+def test_timeout_status_is_reported():
+    """A tile that never publishes: its successor's bounded wait runs out,
+    the launch completes and the result is flagged; the next launch is
+    clean."""
+    sfa = sfa_mod()
+    d = AUTOMATA["r5"]()
+    a = sfa.Automaton.from_dfa(d)
+    t = text_for(d, 100_000, seed=1)
+    import time
+    t0 = time.time()
+    got = gpu_match(a, t, chunk_bytes=16, block_threads=128, chains=1, timeout_us=50_000,
+                    debug_flags=sfa.DEBUG_SKIP_PUBLISH)
+    assert time.time() - t0 < 30
+    assert got[2] == sfa.STATUS_TIMEOUT
+    assert gpu_match(a, t, chunk_bytes=16, block_threads=128, chains=1) == expect(d, t)
+
+
+# ---------------------------------------------------------------------------
+# full-size workloads, in the launch configuration bench.py times
+# ---------------------------------------------------------------------------
+
+def test_full_single_1MiB():
+    d, t = W.workload_single()
+    a = sfa_mod().Automaton.from_dfa(d)
+    got = gpu_match(a, t)
+    assert got == expect(d, t)
+    assert got[3] == oracle.bruteforce_literal_count(d.literals, t) >= 64
+
+
+def test_full_large_1GiB():
+    d, t = W.workload_large()
+    a = sfa_mod().Automaton.from_dfa(d)
+    assert gpu_match(a, t) == expect(d, t)
+
+
+def test_full_simulation_4GiB():
+    t = W.workload_sim_text()
+    tt = torch.from_numpy(t).cuda()
+    for d in W.workload_sim_automata():
+        a = sfa_mod().Automaton.from_dfa(d)
+        out = a.match(tt)
+        torch.cuda.synchronize()
+        got = sfa_mod().decode(out)[0]
+        assert got == expect(d, t), d.name
+    del tt
+
+
+def test_full_batch_4096_texts():
+    from concurrent.futures import ThreadPoolExecutor
+    sfa = sfa_mod()
+    autos_d = W.workload_batch_automata()
+    autos = [sfa.Automaton.from_dfa(d) for d in autos_d]
+    lens = W.workload_batch_lengths()
+    pair = W.workload_batch_pairing(len(lens), len(autos))
+    total = int(lens.sum())
+    big = W.text_uniform(total, W.LOWER_ALPHABET, W.SEED_BATCH + 2)
+    offs = np.concatenate([[0], np.cumsum(lens)])
+    dev = torch.from_numpy(big).cuda()
+    texts = [dev[offs[i]:offs[i + 1]] for i in range(len(lens))]
+    b = sfa.Batch([autos[p] for p in pair], texts)
+    out = b.launch(graph=True)
+    torch.cuda.synchronize()
+    got = sfa.decode(out)
+
+    def ref(i):
+        d = autos_d[pair[i]]
+        return expect(d, big[offs[i]:offs[i + 1]])
+
+    with ThreadPoolExecutor(16) as ex:
+        want = list(ex.map(ref, range(len(lens))))
+    assert got == want

@@ -1,0 +1,222 @@
+"""Host-side logic of the product, on the CPU: the C ABI loads and exports
+every symbol of include/sfa.h, and the D-SFA tables that sfa_compile builds
+agree with the oracle's independent correspondence construction.  No test
+here launches GPU work (handles are compiled host-only)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_1405_0562_gb300 as sfa
+import workloads as W
+from conftest import ROOT
+
+HEADER = os.path.join(ROOT, "include", "sfa.h")
+
+
+def header_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(sfa_[a-z_]+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_symbol():
+    declared = header_functions()
+    assert declared == sorted(sfa.EXPORTED)
+    lib = sfa.lib()
+    for name in declared:
+        assert hasattr(lib, name), name
+
+
+def test_strerror_covers_codes():
+    for code in range(0, -8, -1):
+        assert sfa.strerror(code) != "unknown error code"
+    assert sfa.strerror(-99) == "unknown error code"
+
+
+def host(d, **kw):
+    return sfa.Automaton.from_dfa(d, host_only=True, **kw)
+
+
+def product_maps(a):
+    """Non-constant mappings of the product, in the caller's state numbering,
+    plus the reached constants, as a set of tuples."""
+    info = a.info()
+    nr = info["n_reachable"]
+    orig = a.export(sfa.TABLE_ORIG)
+    maps = a.export(sfa.TABLE_MAPS).reshape(-1, nr) if info["n_nonconst"] else np.zeros((0, nr), np.uint8)
+    return orig, maps
+
+
+def to_orig(vec_kept, orig, nq):
+    """A mapping over kept states (kept numbering) as a mapping over the
+    caller's states (only the reachable ones are defined)."""
+    out = np.full(nq, -1, dtype=np.int64)
+    out[orig] = orig[np.asarray(vec_kept, dtype=np.int64)]
+    return out
+
+
+AUTOMATA = [
+    ("ab_star", W.dfa_ab_star),
+    ("r3", lambda: W.dfa_rn(3)),
+    ("r5", lambda: W.dfa_rn(5)),
+    ("ra2", lambda: W.dfa_ra(2)),
+    ("even_odd5", lambda: W.dfa_even_odd(5)),
+    ("T4", lambda: W.dfa_full_transformation(4)),
+    ("kmp", lambda: W.dfa_kmp(b"abcaab")),
+    ("ac", lambda: W.dfa_aho_corasick([b"he", b"she", b"his", b"hers"])),
+    ("ac_set", lambda: W.literal_set_automaton(11)),
+    ("single", lambda: W.workload_single(1 << 12)[0]),
+]
+
+
+@pytest.mark.parametrize("name,make", AUTOMATA)
+def test_sizes_equal_oracle(name, make):
+    d = make()
+    s = oracle.sfa_build(d.delta)          # over all 256 byte values
+    info = host(d).info()
+    assert info["mode"] == sfa.MODE_SFA
+    assert info["n_reachable"] == d.nq     # generators give accessible DFAs
+    assert info["n_sfa_states"] == s.size
+
+
+@pytest.mark.parametrize("name,make", AUTOMATA)
+def test_tables_equal_oracle_construction(name, make):
+    """Same set of mappings as the oracle, and every row of the product's
+    transition table leads where the oracle's does."""
+    d = make()
+    s = oracle.sfa_build(d.delta)
+    a = host(d)
+    info = a.info()
+    nr, ncls = info["n_reachable"], info["ncls"]
+    orig, maps = product_maps(a)
+    cls = a.export(sfa.TABLE_CLASS)
+    dfa = a.export(sfa.TABLE_DFA).reshape(nr, 256)
+    oracle_ids = {tuple(m): i for i, m in enumerate(s.maps)}
+    prod = {}
+    for k in range(maps.shape[0]):
+        v = tuple(to_orig(maps[k], orig, d.nq))
+        assert v in oracle_ids
+        prod[k] = oracle_ids[v]
+    consts = {oracle_ids[tuple(m)] for m in s.maps if len(set(m.tolist())) == 1}
+    assert len(prod) + len(consts) == s.size
+    # the kept DFA is the caller's DFA renumbered
+    for i in range(nr):
+        assert (orig[dfa[i]] == d.delta[orig[i]]).all()
+    # final states last
+    fa = nr - info["n_accepting"]
+    assert all(d.accept[orig[i]] == (i >= fa) for i in range(nr))
+    if maps.shape[0] == 0:
+        return
+    nc = a.export(sfa.TABLE_NC).reshape(-1, ncls)
+    rng = np.random.default_rng(0)
+    for k in range(maps.shape[0]):
+        for b in rng.integers(0, 256, 24).tolist() + list(d.alphabet):
+            e = int(nc[k, cls[b]])
+            nxt, acc = e & 0x3FFFFFFF, e >> 30
+            want = s.maps[s.delta[prod[k], b]]          # oracle: f . delta^b
+            if nxt < nr:
+                got = np.full(d.nq, orig[nxt])
+                fin = [bool(d.accept[orig[nxt]])]
+            else:
+                got = to_orig(maps[nxt - nr], orig, d.nq)
+                fin = [bool(d.accept[x]) for x in got[orig]]
+            assert (got[orig] == want[orig]).all()
+            assert acc == (1 if all(fin) else (2 if any(fin) else 0))
+
+
+def test_example1_product_numbering():
+    """Constant mappings take the id of their value; the others follow in
+    FIFO order of Alg. 4, f_I first (the numbering of Example 1 minus f3)."""
+    d = W.dfa_ab_star()
+    a = host(d)
+    info = a.info()
+    assert (info["n_sfa_states"], info["n_nonconst"]) == (6, 5)
+    orig, maps = product_maps(a)
+    got = [tuple(to_orig(m, orig, 3)) for m in maps]
+    assert got == [(0, 1, 2), (1, 2, 2), (2, 0, 2), (0, 2, 2), (2, 1, 2)]   # f0 f1 f2 f4 f5
+
+
+def test_printed_sizes_via_product():
+    for n, want in ((5, 109), (50, 10099)):
+        info = host(W.dfa_rn(n)).info()
+        assert info["n_sfa_states"] - 1 == want       # the all-sink map is a constant
+    assert host(W.dfa_even_odd(5)).info()["n_sfa_states"] - 1 == 21
+
+
+def test_cap_switches_to_simulation():
+    d = W.dfa_full_transformation(5)
+    assert host(d, cap_states=100).info()["mode"] == sfa.MODE_SIM
+    info = host(d, cap_states=3125).info()
+    assert info["mode"] == sfa.MODE_SFA and info["n_sfa_states"] == 3125
+    with pytest.raises(sfa.SfaError) as e:
+        host(d, cap_states=100, mode=sfa.MODE_SFA)
+    assert e.value.code == sfa.ERR_UNSUPPORTED
+    assert host(d, mode=sfa.MODE_SIM).info()["mode"] == sfa.MODE_SIM
+
+
+def test_random_dfas_exceed_default_cap():
+    for d in W.workload_sim_automata():
+        info = host(d).info()
+        assert info["mode"] == sfa.MODE_SIM, d.name
+
+
+def test_unreachable_states_are_trimmed():
+    d = W.dfa_ab_star()
+    delta = np.concatenate([d.delta, np.full((2, 256), 3, dtype=np.int32)])   # states 3, 4 unreachable
+    acc = np.concatenate([d.accept, [1, 0]]).astype(np.uint8)
+    a = sfa.Automaton(delta, 0, acc, host_only=True)
+    info = a.info()
+    assert (info["nq"], info["n_reachable"], info["n_sfa_states"]) == (5, 3, 6)
+
+
+@pytest.mark.parametrize("case,code", [
+    ("nq0", sfa.ERR_INVALID), ("nq257", sfa.ERR_UNSUPPORTED), ("range", sfa.ERR_INVALID),
+    ("q0", sfa.ERR_INVALID), ("sim_too_big", sfa.ERR_UNSUPPORTED),
+])
+def test_invalid_dfas(case, code):
+    L = sfa.lib()
+    h = ctypes.c_void_p()
+    opts = sfa.CompileOpts(0, 0, sfa.COMPILE_HOST_ONLY, 0)
+    nq, q0 = 4, 0
+    delta = np.zeros((4, 256), dtype=np.int32)
+    if case == "nq0":
+        nq = 0
+    elif case == "nq257":
+        nq = 257
+        delta = np.zeros((257, 256), dtype=np.int32)
+    elif case == "range":
+        delta[2, 7] = 4
+    elif case == "q0":
+        q0 = 4
+    elif case == "sim_too_big":
+        nq = 80
+        delta = np.tile((np.arange(80, dtype=np.int32)[:, None] + 1) % 80, (1, 256))
+        opts.force_mode = sfa.MODE_SIM
+    acc = np.zeros(max(nq, 1), dtype=np.uint8)
+    rc = L.sfa_compile(delta.ctypes.data, nq, q0, acc.ctypes.data, ctypes.byref(opts), ctypes.byref(h))
+    assert rc == code
+
+
+def test_host_only_handle_refuses_matching():
+    a = host(W.dfa_ab_star())
+    L = sfa.lib()
+    out = ctypes.c_void_p(0)
+    assert L.sfa_match(a.handle, None, 0, ctypes.c_void_p(16), None) == sfa.ERR_HOST_ONLY
+    assert L.sfa_match(a.handle, None, 0, out, None) == sfa.ERR_INVALID   # NULL result pointer
+
+
+def test_class_compression_is_exact():
+    """Bytes in one class have equal columns in the caller's DFA."""
+    d = W.workload_large(1 << 12)[0]
+    a = host(d)
+    cls = a.export(sfa.TABLE_CLASS)
+    for c in np.unique(cls):
+        cols = d.delta[:, cls == c]
+        assert (cols == cols[:, :1]).all()
+    # and different classes differ somewhere
+    reps = [int(np.nonzero(cls == c)[0][0]) for c in np.unique(cls)]
+    assert len({tuple(d.delta[:, b]) for b in reps}) == len(reps)
