@@ -156,14 +156,14 @@ def barrier(world: int):
 # workloads
 # ---------------------------------------------------------------------------
 
-def make_workload(name: str):
+def make_workload(name: str, text_bytes: int = 0):
     if name == "plain_large":
-        d, t = W.workload_large()
+        d, t = W.workload_large(text_bytes or (1 << 30))
         return d, t, {"workload": "plain_large: Aho-Corasick DFA of 16 literals (len 4-12, base64 alphabet), "
                                   "1 GiB Zipf(1.1) text, 1 plant per 64 KiB",
                       "text_bytes": int(t.size), "dfa_states": d.nq, "seed": W.SEED_LARGE}
     if name == "plain_small":
-        d, t = W.workload_single()
+        d, t = W.workload_single(text_bytes or (1 << 20))
         return d, t, {"workload": "plain_small: KMP DFA of one 6-byte literal over a-z (7 states), "
                                   "1 MiB uniform a-z text, 64 plants",
                       "text_bytes": int(t.size), "dfa_states": d.nq, "seed": W.SEED_SINGLE}
@@ -176,7 +176,7 @@ def run_reference(args, rank: int, world: int):
     import oracle
     if rank != 0:
         return
-    d, t, cfg = make_workload(args.workload)
+    d, t, cfg = make_workload(args.workload, args.text_bytes)
     sample = min(t.size, 64 << 20)
     for _ in range(max(args.warmup, 0)):
         oracle.dfa_run(d.delta, d.q0, d.accept, t[:sample])
@@ -217,7 +217,7 @@ def run_gpu(args, rank: int, world: int, local: int):
     import paper_1405_0562_gb300 as sfa
 
     torch.cuda.set_device(local)
-    d, t, cfg = make_workload(args.workload)
+    d, t, cfg = make_workload(args.workload, args.text_bytes)
     a = sfa.Automaton.from_dfa(d)
     info = a.info()
     cfg.update({"sfa_states": info["n_sfa_states"], "byte_classes": info["ncls"],
@@ -309,6 +309,7 @@ def main():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--workload", default="plain_large", choices=["plain_large", "plain_small"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--text-bytes", type=int, default=0, help="override the text size (profiling runs only)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank, world, local = dist_setup(args.gpus)
