@@ -58,6 +58,8 @@ typedef struct sfa_batch *sfa_batch_t;
 #define SFA_ERR_TIMEOUT     -5  /* a device-side bounded wait gave up (see sfa_result.status) */
 #define SFA_ERR_NO_DEVICE   -6  /* no CUDA device is usable */
 #define SFA_ERR_HOST_ONLY   -7  /* the handle was compiled with SFA_COMPILE_HOST_ONLY */
+#define SFA_ERR_SCRATCH_LIMIT -8 /* sfa_match_noalloc: the text needs more scratch than
+                                    the fixed buffer holds */
 
 /* ---- result of one text (16 bytes, written to device memory) ----------- */
 typedef struct {
@@ -206,6 +208,38 @@ int sfa_match_continue(sfa_handle_t h, const uint8_t *d_text, uint64_t n, sfa_re
  */
 int sfa_match_host(sfa_handle_t h, const uint8_t *h_text, uint64_t n, sfa_result *h_out,
                    sfa_stream_t stream, const sfa_launch_opts *opts);
+
+/*
+ * sfa_match_noalloc -- sfa_match for callers that must not allocate device
+ * memory while they match.  Examples: a plugin running inside a host program
+ * that owns all device memory through its own pool and forbids outside
+ * cudaMalloc calls, or a latency-bound loop that cannot afford cudaMalloc /
+ * cudaFree, which may block the host and synchronise the device.
+ * (The paper has no counterpart; this is an interface for such callers.)
+ *
+ * It runs the same D-SFA kernel as sfa_match.  The kernel's scratch (look-back
+ * descriptors, tile aggregates, the per-text record) lives in a fixed
+ * SFA_NOALLOC_SCRATCH_BYTES array compiled into the library instead of in
+ * handle-owned memory; every GPU that loads the library holds one copy until
+ * the process exits.  The caller still passes the text and the result buffer.
+ *   - No cudaMalloc, cudaFree or other allocating call is made.  The first
+ *     call on a device looks up the array's device address (once per device,
+ *     with that device current); make that first call before any stream
+ *     capture.
+ *   - The handle must be in SFA mode (simulation handles: SFA_ERR_UNSUPPORTED)
+ *     and live on the current device (else SFA_ERR_INVALID).
+ *   - A text whose scratch would not fit is rejected with
+ *     SFA_ERR_SCRATCH_LIMIT before any work is enqueued.  The scratch is about
+ *     8 + nr bytes per tile of 512 chunks (nr = reachable states); with the
+ *     automatic chunk sizes texts up to about 30 GB fit for nr = 256.
+ *   - All calls share the one array, and it keeps the last call's contents:
+ *     each call clears the parts that must start at zero.  Calls that overlap
+ *     on the GPU (two streams, two threads, two handles) race on the array and
+ *     give wrong results; issue them on one stream, one after another.
+ */
+#define SFA_NOALLOC_SCRATCH_BYTES (4u << 20)
+int sfa_match_noalloc(sfa_handle_t h, const uint8_t *d_text, uint64_t n, sfa_result *d_out,
+                      sfa_stream_t stream);
 
 /* ---- batches ------------------------------------------------------------- */
 

@@ -23,6 +23,8 @@ LIB_PATH = os.path.join(_PKG, "libsfa.so")
 
 # sfa.h constants
 OK, ERR_INVALID, ERR_UNSUPPORTED, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_NO_DEVICE, ERR_HOST_ONLY = 0, -1, -2, -3, -4, -5, -6, -7
+ERR_SCRATCH_LIMIT = -8
+NOALLOC_SCRATCH_BYTES = 4 << 20
 MODE_AUTO, MODE_SFA, MODE_SIM = 0, 1, 2
 COMPILE_HOST_ONLY = 1
 STATUS_OK, STATUS_TIMEOUT = 0, 1
@@ -35,7 +37,7 @@ EXPORTED = (
     "sfa_compile", "sfa_destroy", "sfa_info", "sfa_export", "sfa_strerror",
     "sfa_match", "sfa_match_ex", "sfa_match_continue", "sfa_match_host",
     "sfa_batch_create", "sfa_batch_launch", "sfa_batch_graph_launch", "sfa_batch_destroy",
-    "sfa_match_batch", "sfa_kernel_launch_count",
+    "sfa_match_batch", "sfa_kernel_launch_count", "sfa_match_noalloc",
 )
 
 
@@ -103,6 +105,7 @@ def lib():
     L.sfa_match_batch.argtypes = [P, P, P, i32, P, P]
     L.sfa_kernel_launch_count.argtypes = []
     L.sfa_kernel_launch_count.restype = u64
+    L.sfa_match_noalloc.argtypes = [P, P, u64, P, P]
     for name in EXPORTED:
         if name not in ("sfa_destroy", "sfa_batch_destroy", "sfa_strerror", "sfa_kernel_launch_count"):
             getattr(L, name).restype = ctypes.c_int
@@ -214,6 +217,16 @@ class Automaton:
         ptr = _dev_ptr(text, "text") if n else 0
         _check(lib().sfa_match_ex(self._h, ptr, n, _dev_ptr(out, "out"), _stream_ptr(stream), ctypes.byref(o)),
                "sfa_match_ex")
+        return out
+
+    def match_noalloc(self, text, out, stream=None):
+        """sfa_match_noalloc: for callers that must not allocate device memory
+        while matching; `out` must be a caller-owned 16-byte CUDA buffer.  Its
+        scratch is the library's one fixed array: do not overlap calls."""
+        n = text.numel()
+        ptr = _dev_ptr(text, "text") if n else 0
+        _check(lib().sfa_match_noalloc(self._h, ptr, n, _dev_ptr(out, "out"), _stream_ptr(stream)),
+               "sfa_match_noalloc")
         return out
 
     def match_continue(self, text, inout, stream=None, **launch):

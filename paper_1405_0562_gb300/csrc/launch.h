@@ -5,6 +5,7 @@
 
 #include <cstddef>
 
+#include "sfa.h"
 #include "sfa_types.h"
 
 namespace sfa_impl {
@@ -17,5 +18,11 @@ const void *kernel_for_sim(int threads, int chains, int simnq);
 
 // Dynamic shared memory of a launch shape.
 size_t smem_bytes(int threads, int chains, uint32_t nr_max);
+
+// The D-SFA match of sfa_match with automatic shape, on a caller-provided
+// scratch buffer of `cap` bytes that lives on device `scratch_device`.
+// Allocates nothing; SFA_ERR_SCRATCH_LIMIT if the launch needs more.
+int match_into_scratch(sfa_handle_t h, const uint8_t *d_text, uint64_t n, sfa_result *d_out, cudaStream_t s,
+                       uint8_t *scratch, size_t cap, int scratch_device);
 
 }  // namespace sfa_impl

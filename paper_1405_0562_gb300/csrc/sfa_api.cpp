@@ -406,6 +406,7 @@ const char *sfa_strerror(int code) {
         case SFA_ERR_TIMEOUT: return "a device-side bounded wait gave up";
         case SFA_ERR_NO_DEVICE: return "no usable CUDA device";
         case SFA_ERR_HOST_ONLY: return "handle has no device tables (compiled host-only)";
+        case SFA_ERR_SCRATCH_LIMIT: return "text needs more scratch than the fixed no-allocation buffer holds";
         default: return "unknown error code";
     }
 }
@@ -727,3 +728,42 @@ int sfa_match_batch(const sfa_handle_t *hs, const uint8_t *const *d_texts, const
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// matching on a fixed, caller-provided scratch buffer (sfa_match_noalloc)
+// ---------------------------------------------------------------------------
+namespace sfa_impl {
+
+int match_into_scratch(sfa_handle_t h, const uint8_t *d_text, uint64_t n, sfa_result *d_out, cudaStream_t s,
+                       uint8_t *scratch, size_t cap, int scratch_device) {
+    if (!h || !d_out || !scratch) return SFA_ERR_INVALID;
+    if (n > MAX_TEXT || (n > 0 && !d_text)) return SFA_ERR_INVALID;
+    if (!h->on_device) return SFA_ERR_HOST_ONLY;
+    if (h->host.mode != SFA_MODE_SFA) return SFA_ERR_UNSUPPORTED;
+    if (h->device != scratch_device) return SFA_ERR_INVALID;
+    Shape sh;
+    int rc = choose_shape(h, n, nullptr, sh);
+    if (rc) return rc;
+    TextDesc d{};
+    d.text = d_text;
+    d.n = n;
+    d.chunk = sh.chunk;
+    d.forced = 0;
+    const uint64_t cpt = (uint64_t)sh.threads * sh.chains;
+    if (sfa_dev::num_chunks(d) >= (1ull << 31) - 256) return SFA_ERR_SCRATCH_LIMIT;
+    const uint64_t tiles = (sfa_dev::num_chunks(d) + cpt - 1) / cpt;
+    d.ntiles = (uint32_t)tiles;
+    const uint32_t nr = h->host.nr;
+    const ScratchPlan p = plan_scratch(1, tiles, nr, 0);
+    if (p.total > cap) return SFA_ERR_SCRATCH_LIMIT;
+    // the buffer keeps the previous call's contents: clear the header, the
+    // text record and the look-back descriptors
+    CK(cudaMemsetAsync(scratch, 0, p.zero, s));
+    const Scratch S = make_scratch(scratch, p, nr, (uint32_t)tiles, sh);
+    const void *k = kernel_for(sh.threads, sh.chains, 0, false);
+    const size_t smem = smem_bytes(sh.threads, sh.chains, nr);
+    return launch_kernel(k, sh.threads, smem, (uint32_t)tiles, 0, s, h->dev, d, nullptr, nullptr, nullptr, S,
+                         d_out);
+}
+
+}  // namespace sfa_impl

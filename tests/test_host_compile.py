@@ -32,7 +32,7 @@ def test_library_exports_every_declared_symbol():
 
 
 def test_strerror_covers_codes():
-    for code in range(0, -8, -1):
+    for code in range(0, -9, -1):
         assert sfa.strerror(code) != "unknown error code"
     assert sfa.strerror(-99) == "unknown error code"
 

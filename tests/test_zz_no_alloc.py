@@ -1,0 +1,82 @@
+"""sfa_match_noalloc: the entry point for callers that cannot allocate device
+memory while matching (a host program that owns all device memory through
+its own pool, or a loop that cannot pay for cudaMalloc/cudaFree).  Its
+output must equal sfa_match's, exactly (integer results, tolerance 0), on
+two calls in a row that reuse the one fixed scratch array.
+
+This file is named so that pytest collects it last."""
+import ctypes
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def sfa():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    import paper_1405_0562_gb300 as m
+    L = m.lib()
+    L.sfa_match_noalloc.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p,
+                                    ctypes.c_void_p]
+    L.sfa_match_noalloc.restype = ctypes.c_int
+    torch.cuda.set_device(0)
+    return m
+
+
+def noalloc(sfa, a, text, out, stream):
+    n = text.numel()
+    return sfa.lib().sfa_match_noalloc(a.handle, text.data_ptr() if n else None, n, out.data_ptr(),
+                                       stream.cuda_stream)
+
+
+def test_noalloc_equals_match_twice(sfa):
+    cases = [W.workload_large(48 << 20), W.workload_single()]
+    d3 = W.dfa_rn(4)
+    t3 = np.frombuffer(b"01235678" * 100_000 + b"0", dtype=np.uint8).copy()
+    t3[::9973] = ord("9")
+    cases.append((d3, t3))
+    stream = torch.cuda.Stream()
+    for d, t in cases:
+        a = sfa.Automaton.from_dfa(d)
+        tt = torch.from_numpy(t).cuda()
+        ref = a.match(tt, stream=stream)
+        stream.synchronize()
+        want = sfa.decode(ref)[0]
+        f, acc, c = oracle.dfa_run(d.delta, d.q0, d.accept, t)
+        assert want == (f, acc, 0, c)
+        for _ in range(2):
+            out = torch.full((16,), 0xAB, dtype=torch.uint8, device="cuda")
+            assert noalloc(sfa, a, tt, out, stream) == sfa.OK
+            stream.synchronize()
+            assert sfa.decode(out)[0] == want
+        # a shorter text right after a longer one: stale descriptors must not leak
+        out = torch.zeros(16, dtype=torch.uint8, device="cuda")
+        assert noalloc(sfa, a, tt[:1000], out, stream) == sfa.OK
+        stream.synchronize()
+        f, acc, c = oracle.dfa_run(d.delta, d.q0, d.accept, t[:1000])
+        assert sfa.decode(out)[0] == (f, acc, 0, c)
+
+
+def test_noalloc_rejects_what_it_cannot_hold(sfa):
+    stream = torch.cuda.Stream()
+    d, t = W.workload_single()
+    a = sfa.Automaton.from_dfa(d)
+    tt = torch.from_numpy(t).cuda()
+    out = torch.zeros(16, dtype=torch.uint8, device="cuda")
+    L = sfa.lib()
+    # 2^40 bytes would need far more than the fixed scratch: rejected on the
+    # host before anything is enqueued (the pointer is never read)
+    rc = L.sfa_match_noalloc(a.handle, tt.data_ptr(), 1 << 40, out.data_ptr(), stream.cuda_stream)
+    assert rc == sfa.ERR_SCRATCH_LIMIT
+    sim = sfa.Automaton.from_dfa(W.workload_sim_automata()[0])
+    assert L.sfa_match_noalloc(sim.handle, tt.data_ptr(), 16, out.data_ptr(), stream.cuda_stream) == \
+        sfa.ERR_UNSUPPORTED
+    assert L.sfa_match_noalloc(a.handle, None, 16, out.data_ptr(), stream.cuda_stream) == sfa.ERR_INVALID
