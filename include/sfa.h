@@ -259,6 +259,32 @@ int sfa_match_noalloc(sfa_handle_t h, const uint8_t *d_text, uint64_t n, sfa_res
 int sfa_batch_create(const sfa_handle_t *hs, const uint8_t *const *d_texts, const uint64_t *lens,
                      int32_t k, const sfa_launch_opts *opts, sfa_batch_t *out);
 
+/*
+ * sfa_batch_reserve -- a plan with capacity but no work list yet, for loops
+ * that launch a different set of texts each time (serving).
+ *   max_texts  texts per launch
+ *   max_tiles  tiles per launch; a text of n bytes takes at most
+ *              1 + n / (threads * chains * chunk_bytes) tiles
+ *   nr_max     largest reachable-state count of the automata to be used
+ *   opts       launch shape; chunk_bytes fixes the chunk length (0 = 1024)
+ * Allocates device memory and pinned staging once (synchronous).  Its
+ * launches read the tile count on the device, so they stay valid (and a
+ * captured graph stays valid) across sfa_batch_update calls.
+ */
+int sfa_batch_reserve(int32_t max_texts, uint64_t max_tiles, uint32_t nr_max, const sfa_launch_opts *opts,
+                      sfa_batch_t *out);
+
+/*
+ * sfa_batch_update -- replaces the work list of a reserved plan by k texts
+ * (same arguments as sfa_batch_create).  Builds it on the host in pinned
+ * staging and enqueues its upload on `stream`; allocates nothing for SFA-mode
+ * handles (simulation-mode texts may grow their handle's scratch).  Issue the
+ * update and the following launch on the same stream.  INVALID when the texts
+ * exceed the plan's capacity or an automaton has more than nr_max states.
+ */
+int sfa_batch_update(sfa_batch_t b, const sfa_handle_t *hs, const uint8_t *const *d_texts, const uint64_t *lens,
+                     int32_t k, sfa_stream_t stream);
+
 /* sfa_batch_launch -- enqueue the planned work; d_out: device, k results in
  * the order of the texts given to sfa_batch_create.  Launches of one plan
  * must not overlap on the GPU. */

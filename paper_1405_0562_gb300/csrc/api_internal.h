@@ -1,0 +1,106 @@
+// Internals shared by the C ABI units (sfa_api.cpp, batch_api.cpp,
+// noalloc.cu): the handle, launch shapes, scratch plans, launch helpers.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstddef>
+#include <cstdint>
+
+#include "host_compile.h"
+#include "launch.h"
+#include "sfa.h"
+
+namespace sfa_impl {
+
+constexpr uint32_t DEFAULT_TIMEOUT_US = 2000000;   // 2 s per device-side wait
+constexpr uint64_t MAX_TEXT = 1ull << 40;
+constexpr uint64_t MAX_CHUNK = 1ull << 31;         // per-chunk counters are 32-bit
+constexpr uint32_t MAX_FORCED = 1u << 20;
+constexpr uint64_t HOST_PIECE = 64ull << 20;       // sfa_match_host copy granularity
+
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+inline int cuda_err(cudaError_t e) {
+    if (e == cudaSuccess) return SFA_OK;
+    if (e == cudaErrorMemoryAllocation) return SFA_ERR_OOM;
+    if (e == cudaErrorNoDevice || e == cudaErrorInsufficientDriver) return SFA_ERR_NO_DEVICE;
+    return SFA_ERR_CUDA;
+}
+
+#define CK(call)                                        \
+    do {                                                \
+        cudaError_t e_ = (call);                        \
+        if (e_ != cudaSuccess) return sfa_impl::cuda_err(e_); \
+    } while (0)
+
+extern std::atomic<uint64_t> g_launches;   // kernels enqueued since load
+
+struct DeviceProps {
+    int sms = 0;
+    size_t smem_optin = 0;
+};
+DeviceProps device_props(int dev);
+
+// resident CTAs per SM for a kernel instance and shared-memory size (cached;
+// also raises the kernel's dynamic shared-memory limit)
+int blocks_per_sm(const void *k, int threads, size_t smem);
+
+struct Shape {
+    int threads = 256;
+    int chains = 2;
+    int simnq = 0;
+    uint64_t chunk = 1024;
+    uint32_t forced = 0;
+    int max_ctas = 0;
+    uint32_t timeout_us = DEFAULT_TIMEOUT_US;
+    uint32_t debug = 0;
+};
+
+inline int simnq_for(uint32_t nr) { return nr <= 16 ? 16 : (nr <= 32 ? 32 : 64); }
+
+// scratch layout of a launch over `ntext` texts and `tiles` tiles
+struct ScratchPlan {
+    size_t off_texts, off_status, off_agg, off_vec, total, zero;
+};
+ScratchPlan plan_scratch(uint32_t ntext, uint64_t tiles, uint32_t nr_max, uint64_t vec_bytes);
+sfa_dev::Scratch make_scratch(uint8_t *base, const ScratchPlan &p, uint32_t nr_max, uint32_t tiles,
+                              const Shape &sh);
+
+}  // namespace sfa_impl
+
+struct sfa_handle {
+    sfa_impl::HostTables host;
+    bool on_device = false;
+    int device = -1;
+    uint8_t *d_tables = nullptr;
+    size_t table_bytes = 0;
+    sfa_dev::Tables dev{};
+    uint8_t *d_scratch = nullptr;
+    size_t scratch_bytes = 0;
+    // sfa_match_host
+    uint8_t *d_stage[2] = {nullptr, nullptr};
+    size_t stage_bytes = 0;
+    sfa_result *d_res = nullptr;
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t ev_copied[2] = {nullptr, nullptr};
+    cudaEvent_t ev_done[2] = {nullptr, nullptr};
+};
+
+namespace sfa_impl {
+
+// launch shape for one text (automatic fields filled in)
+int choose_shape(const sfa_handle *h, uint64_t n, const sfa_launch_opts *o, Shape &sh);
+// grow the handle's scratch to at least `bytes` (may synchronise and cudaMalloc)
+int ensure_scratch(sfa_handle *h, size_t bytes);
+// enqueue one persistent kernel on `s`
+int launch_kernel(const void *k, int threads, size_t smem, uint32_t tiles, int max_ctas, cudaStream_t s,
+                  const sfa_dev::Tables &tab, const sfa_dev::TextDesc &desc, const sfa_dev::Tables *tabs,
+                  const sfa_dev::TextDesc *descs, const uint32_t *tile_text, const sfa_dev::Scratch &S,
+                  sfa_result *out);
+// one text (sfa_match_ex / sfa_match_continue)
+int match_impl(sfa_handle *h, const uint8_t *d_text, uint64_t n, sfa_result *d_out, cudaStream_t s,
+               const sfa_launch_opts *o, bool carry);
+
+}  // namespace sfa_impl

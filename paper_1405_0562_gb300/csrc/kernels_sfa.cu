@@ -8,27 +8,23 @@ namespace sfa_impl {
 using sfa_dev::sfa_match_kernel;
 
 #define SFA_K(T, C, B) reinterpret_cast<const void *>(&sfa_match_kernel<T, C, 0, B>)
+#define SFA_SHAPES(B)                                              \
+    if (threads == 128 && chains == 1) return SFA_K(128, 1, B);    \
+    if (threads == 128 && chains == 2) return SFA_K(128, 2, B);    \
+    if (threads == 128 && chains == 4) return SFA_K(128, 4, B);    \
+    if (threads == 256 && chains == 1) return SFA_K(256, 1, B);    \
+    if (threads == 256 && chains == 2) return SFA_K(256, 2, B);    \
+    if (threads == 256 && chains == 4) return SFA_K(256, 4, B);    \
+    if (threads == 512 && chains == 1) return SFA_K(512, 1, B);    \
+    if (threads == 512 && chains == 2) return SFA_K(512, 2, B);    \
+    if (threads == 1024 && chains == 1) return SFA_K(1024, 1, B);
 
 const void *kernel_for_sfa(int threads, int chains, bool batch) {
     if (batch) {
-        if (threads == 128 && chains == 1) return SFA_K(128, 1, true);
-        if (threads == 128 && chains == 2) return SFA_K(128, 2, true);
-        if (threads == 128 && chains == 4) return SFA_K(128, 4, true);
-        if (threads == 256 && chains == 1) return SFA_K(256, 1, true);
-        if (threads == 256 && chains == 2) return SFA_K(256, 2, true);
-        if (threads == 256 && chains == 4) return SFA_K(256, 4, true);
-        if (threads == 512 && chains == 1) return SFA_K(512, 1, true);
-        if (threads == 512 && chains == 2) return SFA_K(512, 2, true);
+        SFA_SHAPES(true)
         return nullptr;
     }
-    if (threads == 128 && chains == 1) return SFA_K(128, 1, false);
-    if (threads == 128 && chains == 2) return SFA_K(128, 2, false);
-    if (threads == 128 && chains == 4) return SFA_K(128, 4, false);
-    if (threads == 256 && chains == 1) return SFA_K(256, 1, false);
-    if (threads == 256 && chains == 2) return SFA_K(256, 2, false);
-    if (threads == 256 && chains == 4) return SFA_K(256, 4, false);
-    if (threads == 512 && chains == 1) return SFA_K(512, 1, false);
-    if (threads == 512 && chains == 2) return SFA_K(512, 2, false);
+    SFA_SHAPES(false)
     return nullptr;
 }
 
@@ -43,6 +39,7 @@ size_t smem_bytes(int threads, int chains, uint32_t nr_max) {
         case 256 * 8 + 4: return SmemLayout<256, 4>::bytes(nr_max);
         case 512 * 8 + 1: return SmemLayout<512, 1>::bytes(nr_max);
         case 512 * 8 + 2: return SmemLayout<512, 2>::bytes(nr_max);
+        case 1024 * 8 + 1: return SmemLayout<1024, 1>::bytes(nr_max);
         default: return 0;
     }
 }

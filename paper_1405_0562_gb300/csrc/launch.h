@@ -24,5 +24,8 @@ size_t smem_bytes(int threads, int chains, uint32_t nr_max);
 // Allocates nothing; SFA_ERR_SCRATCH_LIMIT if the launch needs more.
 int match_into_scratch(sfa_handle_t h, const uint8_t *d_text, uint64_t n, sfa_result *d_out, cudaStream_t s,
                        uint8_t *scratch, size_t cap, int scratch_device);
+// The checks of match_into_scratch that need no device: arguments, mode and
+// the scratch the text would need (SFA_ERR_SCRATCH_LIMIT).
+int check_into_scratch(sfa_handle_t h, const uint8_t *d_text, uint64_t n, const sfa_result *d_out, size_t cap);
 
 }  // namespace sfa_impl

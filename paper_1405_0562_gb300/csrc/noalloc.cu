@@ -42,10 +42,13 @@ int scratch_address(uint8_t **out, int *dev_out) {
 
 extern "C" int sfa_match_noalloc(sfa_handle_t h, const uint8_t *d_text, uint64_t n, sfa_result *d_out,
                                  sfa_stream_t stream) {
-    if (!h || !d_out || (n > 0 && !d_text)) return SFA_ERR_INVALID;
+    // every check that needs no device first: a text that does not fit is
+    // rejected before anything touches the GPU
+    int rc = sfa_impl::check_into_scratch(h, d_text, n, d_out, SFA_NOALLOC_SCRATCH_BYTES);
+    if (rc) return rc;
     uint8_t *scratch = nullptr;
     int dev = -1;
-    int rc = scratch_address(&scratch, &dev);
+    rc = scratch_address(&scratch, &dev);
     if (rc) return rc;
     return sfa_impl::match_into_scratch(h, d_text, n, d_out, (cudaStream_t)stream, scratch,
                                         SFA_NOALLOC_SCRATCH_BYTES, dev);

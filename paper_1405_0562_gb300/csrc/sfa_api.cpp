@@ -1,52 +1,24 @@
-// C ABI of the matcher (declared in include/sfa.h): handles, device tables,
-// scratch, launch shapes, the streaming host path, batch plans and graphs.
+// C ABI of the matcher for single texts (declared in include/sfa.h):
+// handles, device tables, scratch, launch shapes, the streaming host path.
+// Batches are in batch_api.cpp, the no-allocation entry point in noalloc.cu.
 #include <cuda_runtime.h>
 
 #include <algorithm>
-#include <atomic>
 #include <cstring>
 #include <map>
 #include <mutex>
 #include <new>
 #include <vector>
 
-#include "host_compile.h"
-#include "launch.h"
-#include "sfa.h"
+#include "api_internal.h"
 
 using sfa_dev::Scratch;
 using sfa_dev::Tables;
 using sfa_dev::TextDesc;
 
-namespace {
+namespace sfa_impl {
 
 std::atomic<uint64_t> g_launches{0};
-
-constexpr uint32_t DEFAULT_TIMEOUT_US = 2000000;   // 2 s per device-side wait
-constexpr uint64_t MAX_TEXT = 1ull << 40;
-constexpr uint64_t MAX_CHUNK = 1ull << 31;         // per-chunk counters are 32-bit
-constexpr uint32_t MAX_FORCED = 1u << 20;
-constexpr uint64_t HOST_PIECE = 64ull << 20;       // sfa_match_host copy granularity
-
-size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
-
-int cuda_err(cudaError_t e) {
-    if (e == cudaSuccess) return SFA_OK;
-    if (e == cudaErrorMemoryAllocation) return SFA_ERR_OOM;
-    if (e == cudaErrorNoDevice || e == cudaErrorInsufficientDriver) return SFA_ERR_NO_DEVICE;
-    return SFA_ERR_CUDA;
-}
-
-#define CK(call)                                  \
-    do {                                          \
-        cudaError_t e_ = (call);                  \
-        if (e_ != cudaSuccess) return cuda_err(e_); \
-    } while (0)
-
-struct DeviceProps {
-    int sms = 0;
-    size_t smem_optin = 0;
-};
 
 DeviceProps device_props(int dev) {
     static std::mutex mu;
@@ -62,7 +34,6 @@ DeviceProps device_props(int dev) {
     return p;
 }
 
-// resident CTAs per SM for a kernel instance and shared-memory size
 int blocks_per_sm(const void *k, int threads, size_t smem) {
     static std::mutex mu;
     static std::map<std::pair<const void *, size_t>, int> cache;
@@ -79,43 +50,6 @@ int blocks_per_sm(const void *k, int threads, size_t smem) {
     return b;
 }
 
-struct Shape {
-    int threads = 256;
-    int chains = 2;
-    int simnq = 0;
-    uint64_t chunk = 1024;
-    uint32_t forced = 0;
-    int max_ctas = 0;
-    uint32_t timeout_us = DEFAULT_TIMEOUT_US;
-    uint32_t debug = 0;
-};
-
-int simnq_for(uint32_t nr) { return nr <= 16 ? 16 : (nr <= 32 ? 32 : 64); }
-
-}  // namespace
-
-// ---------------------------------------------------------------------------
-// handle
-// ---------------------------------------------------------------------------
-struct sfa_handle {
-    sfa_impl::HostTables host;
-    bool on_device = false;
-    int device = -1;
-    uint8_t *d_tables = nullptr;
-    size_t table_bytes = 0;
-    Tables dev{};
-    uint8_t *d_scratch = nullptr;
-    size_t scratch_bytes = 0;
-    // sfa_match_host
-    uint8_t *d_stage[2] = {nullptr, nullptr};
-    size_t stage_bytes = 0;
-    sfa_result *d_res = nullptr;
-    cudaStream_t copy_stream = nullptr;
-    cudaEvent_t ev_copied[2] = {nullptr, nullptr};
-    cudaEvent_t ev_done[2] = {nullptr, nullptr};
-};
-
-namespace {
 
 int upload_tables(sfa_handle *h) {
     const auto &H = h->host;
@@ -160,10 +94,6 @@ int upload_tables(sfa_handle *h) {
 }
 
 // scratch layout of a launch over `ntext` texts and `tiles` tiles
-struct ScratchPlan {
-    size_t off_texts, off_status, off_agg, off_vec, total, zero;
-};
-
 ScratchPlan plan_scratch(uint32_t ntext, uint64_t tiles, uint32_t nr_max, uint64_t vec_bytes) {
     ScratchPlan p;
     p.off_texts = sizeof(sfa_dev::LaunchHeader);
@@ -196,6 +126,17 @@ int choose_shape(const sfa_handle *h, uint64_t n, const sfa_launch_opts *o, Shap
     sh.simnq = sim ? simnq_for(h->host.nr) : 0;
     sh.threads = sim ? 128 : 256;
     sh.chains = sim ? 1 : 2;
+    if (!sim) {
+        // the largest CTA (one chunk per thread) whose shared memory fits
+        const size_t optin = device_props(h->device).smem_optin;
+        for (int t : {1024, 512, 256}) {
+            if (optin == 0 || smem_bytes(t, 1, h->host.nr) <= optin) {
+                sh.threads = t;
+                sh.chains = 1;
+                break;
+            }
+        }
+    }
     if (o) {
         if (o->block_threads) sh.threads = (int)o->block_threads;
         if (o->chains) sh.chains = (int)o->chains;
@@ -203,7 +144,7 @@ int choose_shape(const sfa_handle *h, uint64_t n, const sfa_launch_opts *o, Shap
         sh.debug = o->debug_flags;
         sh.max_ctas = (int)o->max_ctas;
     }
-    if (!sfa_impl::kernel_for(sh.threads, sh.chains, sh.simnq, false)) return SFA_ERR_UNSUPPORTED;
+    if (!kernel_for(sh.threads, sh.chains, sh.simnq, false)) return SFA_ERR_UNSUPPORTED;
     const uint64_t cpt = (uint64_t)sh.threads * sh.chains;
     if (o && o->forced_chunks) {
         if (o->forced_chunks > MAX_FORCED) return SFA_ERR_INVALID;
@@ -313,7 +254,9 @@ void free_handle_device(sfa_handle *h) {
     if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
 }
 
-}  // namespace
+}  // namespace sfa_impl
+
+using namespace sfa_impl;
 
 extern "C" {
 
@@ -480,271 +423,22 @@ uint64_t sfa_kernel_launch_count(void) { return g_launches.load(); }
 }  // extern "C"
 
 // ---------------------------------------------------------------------------
-// batches
-// ---------------------------------------------------------------------------
-struct sfa_batch {
-    int device = -1;
-    int32_t k = 0;
-    Shape shape;
-    uint8_t *d_mem = nullptr;           // tables array, descriptors, tile map
-    uint8_t *d_scratch = nullptr;
-    ScratchPlan plan{};
-    Scratch S{};
-    const Tables *d_tabs = nullptr;
-    const TextDesc *d_descs = nullptr;
-    const uint32_t *d_tile_text = nullptr;
-    uint32_t total_tiles = 0;
-    uint32_t nr_max = 0;
-    size_t smem = 0;
-    const void *kernel = nullptr;
-    // texts whose handle is in simulation mode: matched one by one
-    std::vector<int32_t> sim_index;
-    std::vector<sfa_handle_t> sim_handle;
-    std::vector<const uint8_t *> sim_text;
-    std::vector<uint64_t> sim_len;
-    // CUDA graph of the launch, keyed by the output pointer
-    cudaStream_t cap_stream = nullptr;
-    cudaGraphExec_t exec = nullptr;
-    sfa_result *exec_out = nullptr;
-};
-
-namespace {
-
-int batch_enqueue(sfa_batch *b, sfa_result *d_out, cudaStream_t s) {
-    if (b->total_tiles > 0) {
-        CK(cudaMemsetAsync(b->d_scratch, 0, b->plan.zero, s));
-        int rc = launch_kernel(b->kernel, b->shape.threads, b->smem, b->total_tiles, b->shape.max_ctas, s, Tables{},
-                               TextDesc{}, b->d_tabs, b->d_descs, b->d_tile_text, b->S, d_out);
-        if (rc) return rc;
-    }
-    for (size_t i = 0; i < b->sim_index.size(); ++i) {
-        int rc = match_impl(b->sim_handle[i], b->sim_text[i], b->sim_len[i], d_out + b->sim_index[i], s, nullptr,
-                            false);
-        if (rc) return rc;
-    }
-    return SFA_OK;
-}
-
-void batch_free(sfa_batch *b) {
-    if (b->exec) cudaGraphExecDestroy(b->exec);
-    if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
-    if (b->d_mem) cudaFree(b->d_mem);
-    if (b->d_scratch) cudaFree(b->d_scratch);
-}
-
-}  // namespace
-
-extern "C" {
-
-int sfa_batch_create(const sfa_handle_t *hs, const uint8_t *const *d_texts, const uint64_t *lens, int32_t k,
-                     const sfa_launch_opts *opts, sfa_batch_t *out) {
-    if (!out || k < 0 || (k > 0 && (!hs || !d_texts || !lens))) return SFA_ERR_INVALID;
-    *out = nullptr;
-    int dev = 0;
-    CK(cudaGetDevice(&dev));
-    sfa_batch *b = new (std::nothrow) sfa_batch();
-    if (!b) return SFA_ERR_OOM;
-    b->device = dev;
-    b->k = k;
-    Shape &sh = b->shape;
-    sh.threads = 256;
-    sh.chains = 2;
-    if (opts) {
-        if (opts->block_threads) sh.threads = (int)opts->block_threads;
-        if (opts->chains) sh.chains = (int)opts->chains;
-        if (opts->timeout_us) sh.timeout_us = opts->timeout_us;
-        sh.debug = opts->debug_flags;
-        sh.max_ctas = (int)opts->max_ctas;
-    }
-    b->kernel = sfa_impl::kernel_for(sh.threads, sh.chains, 0, true);
-    if (!b->kernel) {
-        delete b;
-        return SFA_ERR_UNSUPPORTED;
-    }
-    const uint64_t cpt = (uint64_t)sh.threads * sh.chains;
-    // texts in SFA mode, grouped by automaton (stable in text order)
-    std::vector<int32_t> order;
-    std::vector<sfa_handle_t> distinct;
-    std::map<sfa_handle_t, uint32_t> tab_of;
-    uint64_t total_bytes = 0;
-    for (int32_t i = 0; i < k; ++i) {
-        sfa_handle_t h = hs[i];
-        if (!h || !h->on_device || h->device != dev || lens[i] > MAX_TEXT || (lens[i] && !d_texts[i])) {
-            delete b;
-            return h && !h->on_device ? SFA_ERR_HOST_ONLY : SFA_ERR_INVALID;
-        }
-        if (h->host.mode == SFA_MODE_SIM) {
-            b->sim_index.push_back(i);
-            b->sim_handle.push_back(h);
-            b->sim_text.push_back(d_texts[i]);
-            b->sim_len.push_back(lens[i]);
-            continue;
-        }
-        if (!tab_of.count(h)) {
-            tab_of[h] = (uint32_t)distinct.size();
-            distinct.push_back(h);
-            b->nr_max = std::max<uint32_t>(b->nr_max, (uint32_t)h->host.nr);
-        }
-        order.push_back(i);
-        total_bytes += lens[i];
-    }
-    std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) { return tab_of[hs[x]] < tab_of[hs[y]]; });
-    b->smem = sfa_impl::smem_bytes(sh.threads, sh.chains, std::max<uint32_t>(b->nr_max, 1));
-    // chunk length: as for one text of the batch's total size, shortened
-    // for texts that would not fill a tile
-    uint64_t chunk = opts && opts->chunk_bytes ? opts->chunk_bytes : 0;
-    const int bps = blocks_per_sm(b->kernel, sh.threads, b->smem);   // also caches it before any capture
-    if (!chunk) {
-        const uint64_t ctas = (uint64_t)std::max(1, bps) * std::max(1, device_props(dev).sms);
-        chunk = std::min<uint64_t>(4096, std::max<uint64_t>(256, align_up(total_bytes / (ctas * 6 * cpt), 16)));
-    }
-    if (chunk > MAX_CHUNK) {
-        delete b;
-        return SFA_ERR_INVALID;
-    }
-    std::vector<TextDesc> descs;
-    std::vector<uint32_t> tile_text;
-    for (int32_t i : order) {
-        TextDesc d{};
-        d.text = d_texts[i];
-        d.n = lens[i];
-        uint64_t want = align_up((d.n + cpt - 1) / cpt, 16);
-        d.chunk = std::min<uint64_t>(chunk, std::max<uint64_t>(64, want));
-        d.forced = 0;
-        const uint64_t t = (sfa_dev::num_chunks(d) + cpt - 1) / cpt;
-        d.ntiles = (uint32_t)t;
-        d.tile_base = (uint32_t)tile_text.size();
-        d.table = tab_of[hs[i]];
-        d.out_index = (uint32_t)i;
-        d.carry = 0;
-        if (sfa_dev::num_chunks(d) >= (1ull << 31) || tile_text.size() + t >= (1ull << 30)) {
-            delete b;
-            return SFA_ERR_INVALID;
-        }
-        for (uint64_t j = 0; j < t; ++j) tile_text.push_back((uint32_t)descs.size());
-        descs.push_back(d);
-    }
-    b->total_tiles = (uint32_t)tile_text.size();
-    std::vector<Tables> tabs;
-    for (auto h : distinct) tabs.push_back(h->dev);
-    const size_t off_tabs = 0;
-    const size_t off_descs = align_up(off_tabs + tabs.size() * sizeof(Tables), 256);
-    const size_t off_tt = align_up(off_descs + descs.size() * sizeof(TextDesc), 256);
-    const size_t mem = align_up(off_tt + tile_text.size() * 4, 256) + 256;
-    std::vector<uint8_t> img(mem, 0);
-    if (!tabs.empty()) std::memcpy(img.data() + off_tabs, tabs.data(), tabs.size() * sizeof(Tables));
-    if (!descs.empty()) std::memcpy(img.data() + off_descs, descs.data(), descs.size() * sizeof(TextDesc));
-    if (!tile_text.empty()) std::memcpy(img.data() + off_tt, tile_text.data(), tile_text.size() * 4);
-    cudaError_t e = cudaMalloc(&b->d_mem, mem);
-    if (e == cudaSuccess) e = cudaMemcpy(b->d_mem, img.data(), mem, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) {
-        b->plan = plan_scratch((uint32_t)std::max<size_t>(descs.size(), 1), b->total_tiles, std::max<uint32_t>(b->nr_max, 1), 0);
-        e = cudaMalloc(&b->d_scratch, b->plan.total);
-    }
-    if (e != cudaSuccess) {
-        batch_free(b);
-        delete b;
-        return cuda_err(e);
-    }
-    b->d_tabs = reinterpret_cast<const Tables *>(b->d_mem + off_tabs);
-    b->d_descs = reinterpret_cast<const TextDesc *>(b->d_mem + off_descs);
-    b->d_tile_text = reinterpret_cast<const uint32_t *>(b->d_mem + off_tt);
-    b->S = make_scratch(b->d_scratch, b->plan, std::max<uint32_t>(b->nr_max, 1), b->total_tiles, sh);
-    // simulation-mode texts: size their handles' scratch now, so that
-    // launches (and graph captures) of the plan never allocate
-    for (size_t i = 0; i < b->sim_index.size(); ++i) {
-        Shape ss;
-        int rc = choose_shape(b->sim_handle[i], b->sim_len[i], nullptr, ss);
-        if (!rc) {
-            TextDesc d{};
-            d.n = b->sim_len[i];
-            d.chunk = ss.chunk;
-            const uint64_t c2 = (uint64_t)ss.threads * ss.chains;
-            const uint64_t t = (sfa_dev::num_chunks(d) + c2 - 1) / c2;
-            rc = ensure_scratch(b->sim_handle[i], plan_scratch(1, t, b->sim_handle[i]->host.nr,
-                                                               t * c2 * b->sim_handle[i]->host.nr).total);
-        }
-        if (rc) {
-            batch_free(b);
-            delete b;
-            return rc;
-        }
-    }
-    *out = b;
-    return SFA_OK;
-}
-
-int sfa_batch_launch(sfa_batch_t b, sfa_result *d_out, sfa_stream_t stream) {
-    if (!b || (b->k > 0 && !d_out)) return SFA_ERR_INVALID;
-    return batch_enqueue(b, d_out, (cudaStream_t)stream);
-}
-
-int sfa_batch_graph_launch(sfa_batch_t b, sfa_result *d_out, sfa_stream_t stream) {
-    if (!b || (b->k > 0 && !d_out)) return SFA_ERR_INVALID;
-    if (!b->exec || b->exec_out != d_out) {
-        if (b->exec) {
-            CK(cudaStreamSynchronize((cudaStream_t)stream));
-            cudaGraphExecDestroy(b->exec);
-            b->exec = nullptr;
-        }
-        if (!b->cap_stream) CK(cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking));
-        CK(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
-        const uint64_t before = g_launches.load();
-        int rc = batch_enqueue(b, d_out, b->cap_stream);
-        g_launches.store(before);   // captured, not launched
-        cudaGraph_t g = nullptr;
-        cudaError_t e = cudaStreamEndCapture(b->cap_stream, &g);
-        if (rc) {
-            if (g) cudaGraphDestroy(g);
-            return rc;
-        }
-        if (e != cudaSuccess) return cuda_err(e);
-        e = cudaGraphInstantiate(&b->exec, g, 0);
-        cudaGraphDestroy(g);
-        if (e != cudaSuccess) return cuda_err(e);
-        b->exec_out = d_out;
-    }
-    CK(cudaGraphLaunch(b->exec, (cudaStream_t)stream));
-    g_launches.fetch_add((b->total_tiles > 0 ? 1 : 0) + b->sim_index.size(), std::memory_order_relaxed);
-    return SFA_OK;
-}
-
-void sfa_batch_destroy(sfa_batch_t b) {
-    if (!b) return;
-    batch_free(b);
-    delete b;
-}
-
-int sfa_match_batch(const sfa_handle_t *hs, const uint8_t *const *d_texts, const uint64_t *lens, int32_t k,
-                    sfa_result *d_out, sfa_stream_t stream) {
-    sfa_batch_t b = nullptr;
-    int rc = sfa_batch_create(hs, d_texts, lens, k, nullptr, &b);
-    if (rc) return rc;
-    rc = sfa_batch_launch(b, d_out, stream);
-    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
-    sfa_batch_destroy(b);
-    if (rc) return rc;
-    return cuda_err(e);
-}
-
-}  // extern "C"
-
-// ---------------------------------------------------------------------------
 // matching on a fixed, caller-provided scratch buffer (sfa_match_noalloc)
 // ---------------------------------------------------------------------------
 namespace sfa_impl {
 
-int match_into_scratch(sfa_handle_t h, const uint8_t *d_text, uint64_t n, sfa_result *d_out, cudaStream_t s,
-                       uint8_t *scratch, size_t cap, int scratch_device) {
-    if (!h || !d_out || !scratch) return SFA_ERR_INVALID;
+namespace {
+
+// Host-side part of sfa_match_noalloc: argument checks, launch shape and the
+// scratch it needs, all decided before any work is enqueued.
+int plan_into_scratch(sfa_handle_t h, const uint8_t *d_text, uint64_t n, const sfa_result *d_out, size_t cap,
+                      Shape &sh, TextDesc &d, ScratchPlan &p) {
+    if (!h || !d_out) return SFA_ERR_INVALID;
     if (n > MAX_TEXT || (n > 0 && !d_text)) return SFA_ERR_INVALID;
-    if (!h->on_device) return SFA_ERR_HOST_ONLY;
     if (h->host.mode != SFA_MODE_SFA) return SFA_ERR_UNSUPPORTED;
-    if (h->device != scratch_device) return SFA_ERR_INVALID;
-    Shape sh;
     int rc = choose_shape(h, n, nullptr, sh);
     if (rc) return rc;
-    TextDesc d{};
+    d = TextDesc{};
     d.text = d_text;
     d.n = n;
     d.chunk = sh.chunk;
@@ -753,9 +447,32 @@ int match_into_scratch(sfa_handle_t h, const uint8_t *d_text, uint64_t n, sfa_re
     if (sfa_dev::num_chunks(d) >= (1ull << 31) - 256) return SFA_ERR_SCRATCH_LIMIT;
     const uint64_t tiles = (sfa_dev::num_chunks(d) + cpt - 1) / cpt;
     d.ntiles = (uint32_t)tiles;
-    const uint32_t nr = h->host.nr;
-    const ScratchPlan p = plan_scratch(1, tiles, nr, 0);
+    p = plan_scratch(1, tiles, h->host.nr, 0);
     if (p.total > cap) return SFA_ERR_SCRATCH_LIMIT;
+    return SFA_OK;
+}
+
+}  // namespace
+
+int check_into_scratch(sfa_handle_t h, const uint8_t *d_text, uint64_t n, const sfa_result *d_out, size_t cap) {
+    Shape sh;
+    TextDesc d;
+    ScratchPlan p;
+    return plan_into_scratch(h, d_text, n, d_out, cap, sh, d, p);
+}
+
+int match_into_scratch(sfa_handle_t h, const uint8_t *d_text, uint64_t n, sfa_result *d_out, cudaStream_t s,
+                       uint8_t *scratch, size_t cap, int scratch_device) {
+    Shape sh;
+    TextDesc d;
+    ScratchPlan p;
+    int rc = plan_into_scratch(h, d_text, n, d_out, cap, sh, d, p);
+    if (rc) return rc;
+    if (!scratch) return SFA_ERR_INVALID;
+    if (!h->on_device) return SFA_ERR_HOST_ONLY;
+    if (h->device != scratch_device) return SFA_ERR_INVALID;
+    const uint64_t tiles = d.ntiles;
+    const uint32_t nr = h->host.nr;
     // the buffer keeps the previous call's contents: clear the header, the
     // text record and the look-back descriptors
     CK(cudaMemsetAsync(scratch, 0, p.zero, s));

@@ -10,6 +10,12 @@
 //            (its SFA row is the DFA row of c), id >= nr a non-constant one
 //   group    32 consecutive chunks of a tile (one warp, one round)
 //
+// Text staging: a chunk's 16-byte-aligned body arrives in shared memory by
+// bulk asynchronous copies (cp.async.bulk, completed on one mbarrier per warp
+// and stage), SLICE bytes per copy and STAGES copies in flight; the unaligned
+// head and tail bytes are read singly.  The copies bypass the load/store data
+// path, which the table lookups need for themselves.
+//
 // Acceptance bookkeeping (the count): while a chunk runs from f_I its state
 // f is known only as a mapping, so for position j the final-ness of
 // f(s_in) depends on the still unknown entering state s_in exactly when f is
@@ -28,7 +34,7 @@
 namespace sfa_dev {
 
 // ---------------------------------------------------------------------------
-// memory-model helpers
+// memory-model, timer and async-copy helpers
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ uint64_t ld_acquire(const uint64_t *p) {
     uint64_t v;
@@ -45,6 +51,44 @@ __device__ __forceinline__ uint64_t globaltimer() {
 }
 __device__ __forceinline__ uint4 ldg128(const uint8_t *p) {
     return __ldg(reinterpret_cast<const uint4 *>(p));
+}
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_init_fence() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// global -> shared bulk copy of `bytes` (multiple of 16, both addresses
+// 16-byte aligned), completing `bytes` transactions on the mbarrier
+__device__ __forceinline__ void bulk_copy(uint32_t dst, const uint8_t *src, uint32_t bytes, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+        "l"(src), "r"(bytes), "r"(bar)
+        : "memory");
+}
+// hint: bring [src, src + bytes) into L2 (16-byte aligned, multiple of 16)
+__device__ __forceinline__ void bulk_prefetch_l2(const uint8_t *src, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
 // Bounded wait for a non-zero descriptor.  Gives up after timeout_us (wall
@@ -69,6 +113,22 @@ static __device__ __noinline__ uint64_t wait_descriptor(const uint64_t *p, uint3
     }
 }
 
+// Bounded wait for the completion of an mbarrier phase (a stage of bulk
+// copies).  On giving up (timeout_us, or 2^24 polls) it raises the launch
+// error and returns; the stage's bytes are then not trusted.
+static __device__ __noinline__ void wait_stage(uint32_t bar, uint32_t parity, uint32_t *err, uint32_t timeout_us) {
+    if (mbar_try_wait(bar, parity)) return;
+    const uint64_t t0 = globaltimer();
+    const uint64_t limit = (uint64_t)timeout_us * 1000ull;
+    for (uint32_t it = 1;; ++it) {
+        if (mbar_try_wait(bar, parity)) return;
+        if ((it & 63u) == 0 && (globaltimer() - t0 > limit || it > (1u << 24))) {
+            atomicOr(err, 1u);
+            return;
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // per-chunk state of pass 1
 // ---------------------------------------------------------------------------
@@ -78,6 +138,9 @@ struct Chain {
     uint32_t snap;    // cnt at the last mixed position
     int32_t lm;       // offset of the last mixed position, -1 if none
 };
+
+// offset of (state q, byte b) in the shared-memory DFA rows
+__device__ __forceinline__ uint32_t didx(uint32_t q, uint32_t b) { return q * ROWB + b; }
 
 // one symbol of Alg. 5 in the D-SFA: f <- delta_s[f, sigma]
 __device__ __forceinline__ void sfa_step(Chain &s, uint32_t b, int32_t j, const uint8_t *s_dfa,
@@ -94,18 +157,17 @@ __device__ __forceinline__ void sfa_step(Chain &s, uint32_t b, int32_t j, const 
             s.snap = s.cnt;
         }
     } else {
-        s.f = s_dfa[(s.f << 8) | b];
+        s.f = s_dfa[didx(s.f, b)];
         s.cnt += s.f >= first_accept;
     }
 }
 
-// 16 symbols of a constant-state chunk: the DFA row lookups.  The table
-// offset (q << 8) | byte is one byte permute of the text word and q.
+// 4 symbols (one text word) of a constant-state chunk: the DFA row lookups
 __device__ __forceinline__ void dfa_word(uint32_t &q, uint32_t &cnt, uint32_t w, const uint8_t *s_dfa,
                                          uint32_t first_accept) {
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-        q = s_dfa[__byte_perm(w, q, 0x5540 | j)];
+        q = s_dfa[q * ROWB + __byte_perm(w, 0, 0x4440 | j)];
         cnt += q >= first_accept;
     }
 }
@@ -125,10 +187,10 @@ __device__ __forceinline__ void sim_step(SimVec<NQ> &T, Chain &s, uint32_t b, in
 #pragma unroll
     for (int i = 0; i < NQ / 4; ++i) {
         const uint32_t x = T.w[i];
-        const uint32_t y0 = s_dfa[__byte_perm(x, b, 0x5504)];
-        const uint32_t y1 = s_dfa[__byte_perm(x, b, 0x5514)];
-        const uint32_t y2 = s_dfa[__byte_perm(x, b, 0x5524)];
-        const uint32_t y3 = s_dfa[__byte_perm(x, b, 0x5534)];
+        const uint32_t y0 = s_dfa[__byte_perm(x, 0, 0x4440) * ROWB + b];
+        const uint32_t y1 = s_dfa[__byte_perm(x, 0, 0x4441) * ROWB + b];
+        const uint32_t y2 = s_dfa[__byte_perm(x, 0, 0x4442) * ROWB + b];
+        const uint32_t y3 = s_dfa[__byte_perm(x, 0, 0x4443) * ROWB + b];
         const uint32_t y = __byte_perm(__byte_perm(y0, y1, 0x0040), __byte_perm(y2, y3, 0x0040), 0x5410);
         T.w[i] = y;
         mn = __vminu4(mn, y);
@@ -165,7 +227,7 @@ __device__ __forceinline__ uint32_t dfa_count(const uint8_t *text, uint64_t p, u
                                               const uint8_t *s_dfa, uint32_t first_accept) {
     uint32_t c = 0;
     while (p < e && (reinterpret_cast<uintptr_t>(text + p) & 15)) {
-        q = s_dfa[(q << 8) | text[p]];
+        q = s_dfa[didx(q, text[p])];
         c += q >= first_accept;
         ++p;
     }
@@ -177,7 +239,7 @@ __device__ __forceinline__ uint32_t dfa_count(const uint8_t *text, uint64_t p, u
         dfa_word(q, c, v.w, s_dfa, first_accept);
     }
     for (; p < e; ++p) {
-        q = s_dfa[(q << 8) | text[p]];
+        q = s_dfa[didx(q, text[p])];
         c += q >= first_accept;
     }
     return c;
@@ -195,7 +257,8 @@ __global__ void __launch_bounds__(THREADS)
                      const uint32_t *tile_text, Scratch S, sfa_result *out) {
     using L = SmemLayout<THREADS, CH>;
     constexpr int CPT = L::CPT, NW = L::NW, G = L::G;
-    extern __shared__ __align__(16) uint8_t smem[];
+    constexpr int NQ = SIMNQ > 0 ? SIMNQ : 4;
+    extern __shared__ __align__(128) uint8_t smem[];
     const uint32_t nr_max = S.nr_max;
     uint8_t *s_dfa = smem + L::dfa_off();
     uint8_t *s_cls = smem + L::cls_off(nr_max);
@@ -207,6 +270,14 @@ __global__ void __launch_bounds__(THREADS)
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t lanemask_lt = (1u << lane) - 1u;
+    // this warp's stage barriers and this lane's staging rows
+    const uint32_t bar0 = smem_addr(smem + L::bar_off(nr_max)) + (uint32_t)warp * STAGES * 8;
+    uint8_t *rows = smem + L::stage_off(nr_max) + (size_t)warp * STAGES * CH * 32 * SROW;
+    if (lane == 0)
+        for (int s = 0; s < STAGES; ++s) mbar_init(bar0 + 8 * s, 1);
+    mbar_init_fence();
+    __syncwarp();
+    uint32_t parity = 0;             // bit s: phase parity expected next on stage s (warp-uniform)
     uint32_t loaded = 0xffffffffu;   // table index in shared memory (CTA-uniform)
 
     for (;;) {
@@ -216,18 +287,21 @@ __global__ void __launch_bounds__(THREADS)
         }
         __syncthreads();
         const uint32_t gt = s_misc->tile;
-        if (gt >= S.total_tiles) break;
+        // a batch reads its tile count from the work list (tile_text[0]), so a
+        // plan can be refilled without changing its launch
+        const uint32_t total = BATCH ? __ldg(tile_text) : S.total_tiles;
+        if (gt >= total) break;
 
         uint32_t ti = 0;
-        if (BATCH) ti = __ldg(tile_text + gt);
+        if (BATCH) ti = __ldg(tile_text + 1 + gt);
         const TextDesc d = BATCH ? descs[ti] : desc;
         const Tables T = BATCH ? tabs[d.table] : tab;
         const uint32_t tabidx = BATCH ? d.table : 0u;
         if (tabidx != loaded) {
-            // stage the DFA rows and the class table in shared memory
-            const uint4 *src = reinterpret_cast<const uint4 *>(T.dfa);
-            uint4 *dst = reinterpret_cast<uint4 *>(s_dfa);
-            for (uint32_t i = tid; i < T.nr * 16; i += THREADS) dst[i] = __ldg(src + i);
+            // stage the DFA rows (ROWB apart) and the class table
+            const uint32_t *src = reinterpret_cast<const uint32_t *>(T.dfa);
+            for (uint32_t i = tid; i < T.nr * 64; i += THREADS)
+                *reinterpret_cast<uint32_t *>(s_dfa + (i >> 6) * ROWB + (i & 63) * 4) = __ldg(src + i);
             if (tid < 16) reinterpret_cast<uint4 *>(s_cls)[tid] = __ldg(reinterpret_cast<const uint4 *>(T.cls) + tid);
             loaded = tabidx;
             __syncthreads();
@@ -238,10 +312,13 @@ __global__ void __launch_bounds__(THREADS)
         TextState *ts = S.texts + (BATCH ? ti : 0u);
         const uint8_t *text = d.text;
         const uint8_t *mtab = SIMNQ ? S.chainvec : T.maps;
+        const uintptr_t tbase = reinterpret_cast<uintptr_t>(text);
 
         // ---------------- pass 1: every chunk from f_I ----------------
         Chain ch[CH];
-        uint64_t lo[CH], hi[CH];
+        SimVec<NQ> V[CH];
+        bool con[CH];                // simulation: the vector is constant
+        uint64_t lo[CH], hi[CH], ba[CH], bb[CH];
 #pragma unroll
         for (int c = 0; c < CH; ++c) {
             const uint64_t k = (uint64_t)local * CPT + (uint64_t)c * THREADS + tid;
@@ -254,153 +331,179 @@ __global__ void __launch_bounds__(THREADS)
                 lo[c] = k * d.chunk;
                 hi[c] = lo[c] + d.chunk < d.n ? lo[c] + d.chunk : d.n;
             }
+            // body: the 16-byte-aligned addresses inside [lo, hi)
+            const uint64_t a = (((tbase + lo[c]) + 15) & ~(uintptr_t)15) - tbase;
+            const uint64_t b = ((tbase + hi[c]) & ~(uintptr_t)15) - tbase;
+            ba[c] = a < hi[c] ? a : hi[c];
+            bb[c] = b > ba[c] ? b : ba[c];
             ch[c].f = T.ident;
             ch[c].cnt = 0;
             ch[c].snap = 0;
             ch[c].lm = -1;
-        }
-        uint64_t pos[CH];
-#pragma unroll
-        for (int c = 0; c < CH; ++c) {
-            uint64_t p = lo[c];
-            const uint64_t e = hi[c];
-            Chain s = ch[c];
-            if (SIMNQ == 0) {
-                // head bytes until 16-byte alignment, then whole words while
-                // the mapping is not constant
-                while (p < e && (reinterpret_cast<uintptr_t>(text + p) & 15)) {
-                    sfa_step(s, text[p], (int32_t)(p - lo[c]), s_dfa, s_cls, T.nc, nr, T.ncls, A);
-                    ++p;
-                }
-                while (s.f >= nr && p + 16 <= e) {
-                    const uint4 v = ldg128(text + p);
-                    const uint32_t ws[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-                    for (int i = 0; i < 16; ++i)
-                        sfa_step(s, (ws[i >> 2] >> (8 * (i & 3))) & 0xffu, (int32_t)(p - lo[c]) + i, s_dfa,
-                                 s_cls, T.nc, nr, T.ncls, A);
-                    p += 16;
-                }
-                if (s.f >= nr)
-                    for (; p < e; ++p)
-                        sfa_step(s, text[p], (int32_t)(p - lo[c]), s_dfa, s_cls, T.nc, nr, T.ncls, A);
-            } else {
-                constexpr int NQ = SIMNQ > 0 ? SIMNQ : 4;
-                SimVec<NQ> V;
+            con[c] = nr == 1;
+            if (SIMNQ) {
 #pragma unroll
                 for (int i = 0; i < NQ / 4; ++i) {
                     uint32_t w = 0;
 #pragma unroll
-                    for (int b = 0; b < 4; ++b) {
-                        const uint32_t q = 4 * i + b;
-                        w |= (q < nr ? q : 0u) << (8 * b);
+                    for (int b4 = 0; b4 < 4; ++b4) {
+                        const uint32_t q = 4 * i + b4;
+                        w |= (q < nr ? q : 0u) << (8 * b4);
                     }
-                    V.w[i] = w;
+                    V[c].w[i] = w;
                 }
-                bool con = nr == 1;
-                while (!con && p < e && (reinterpret_cast<uintptr_t>(text + p) & 15)) {
-                    sim_step<NQ>(V, s, text[p], (int32_t)(p - lo[c]), s_dfa, A);
-                    ++p;
-                    con = sim_constant<NQ>(V);
-                }
-                while (!con && p + 16 <= e) {
-                    const uint4 v = ldg128(text + p);
-                    const uint32_t ws[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-                    for (int i = 0; i < 16; ++i)
-                        sim_step<NQ>(V, s, (ws[i >> 2] >> (8 * (i & 3))) & 0xffu, (int32_t)(p - lo[c]) + i,
-                                     s_dfa, A);
-                    p += 16;
-                    con = sim_constant<NQ>(V);
-                }
-                while (!con && p < e) {
-                    sim_step<NQ>(V, s, text[p], (int32_t)(p - lo[c]), s_dfa, A);
-                    ++p;
-                    con = sim_constant<NQ>(V);
-                }
-                if (con) {
-                    s.f = V.w[0] & 0xffu;
-                } else {
-                    // keep the vector for the scan: id nr + global chunk index
-                    const uint64_t gk = (uint64_t)gt * CPT + (uint64_t)c * THREADS + tid;
-                    uint8_t *dst = S.chainvec + gk * nr;
-#pragma unroll
-                    for (int i = 0; i < NQ / 4; ++i)
-#pragma unroll
-                        for (int b = 0; b < 4; ++b)
-                            if ((uint32_t)(4 * i + b) < nr) dst[4 * i + b] = (V.w[i] >> (8 * b)) & 0xffu;
-                    s.f = nr + (uint32_t)gk;
-                }
+                if (con[c]) ch[c].f = 0;
             }
-            // a constant chunk now only needs the DFA rows: reach 16-byte
-            // alignment for the fast loop (simulation chunks can converge at
-            // any byte, and a one-state automaton starts constant)
-            if (s.f < nr) {
-                while (p < e && (reinterpret_cast<uintptr_t>(text + p) & 15)) {
-                    s.f = s_dfa[(s.f << 8) | text[p]];
-                    s.cnt += s.f >= A;
-                    ++p;
+        }
+
+        // one symbol of either mode
+        auto step = [&](int c, uint32_t b, int32_t j) {
+            if (SIMNQ) {
+                if (!con[c]) {
+                    sim_step<NQ>(V[c], ch[c], b, j, s_dfa, A);
+                    con[c] = sim_constant<NQ>(V[c]);
+                    if (con[c]) ch[c].f = V[c].w[0] & 0xffu;
+                } else {
+                    ch[c].f = s_dfa[didx(ch[c].f, b)];
+                    ch[c].cnt += ch[c].f >= A;
                 }
             } else {
-                p = e;
+                sfa_step(ch[c], b, j, s_dfa, s_cls, T.nc, nr, T.ncls, A);
             }
-            ch[c] = s;
-            pos[c] = p;
+        };
+        auto constant = [&](int c) -> bool { return SIMNQ ? con[c] : ch[c].f < nr; };
+
+        // head bytes
+#pragma unroll
+        for (int c = 0; c < CH; ++c)
+            for (uint64_t p = lo[c]; p < ba[c]; ++p) step(c, text[p], (int32_t)(p - lo[c]));
+
+        // body: slices through shared memory
+        uint32_t nsl_c[CH];
+        uint32_t nsl = 0;
+#pragma unroll
+        for (int c = 0; c < CH; ++c) {
+            nsl_c[c] = (uint32_t)((bb[c] - ba[c] + SLICE - 1) / SLICE);
+            nsl = nsl_c[c] > nsl ? nsl_c[c] : nsl;
         }
-        // fast loop: all chunks of the thread in lockstep, one DFA lookup per
-        // byte, 16-byte loads prefetched one iteration ahead
-        {
-            uint64_t m = ~0ull;
+        nsl = __reduce_max_sync(0xffffffffu, nsl);
+        auto issue = [&](uint32_t s) {
+            const uint32_t st = s % STAGES;
+            uint32_t sz[CH], tot = 0;
 #pragma unroll
             for (int c = 0; c < CH; ++c) {
-                const uint64_t v = (hi[c] - pos[c]) >> 4;
-                m = v < m ? v : m;
+                const uint64_t off = ba[c] + (uint64_t)s * SLICE;
+                sz[c] = s < nsl_c[c] ? (uint32_t)(bb[c] - off < (uint64_t)SLICE ? bb[c] - off : SLICE) : 0u;
+                tot += sz[c];
             }
-            uint32_t q[CH], cn[CH];
+            tot = __reduce_add_sync(0xffffffffu, tot);
+            if (lane == 0) mbar_arrive_expect_tx(bar0 + 8 * st, tot);
+            __syncwarp();
+            fence_proxy_async_smem();
+#pragma unroll
+            for (int c = 0; c < CH; ++c)
+                if (sz[c])
+                    bulk_copy(smem_addr(rows + ((size_t)(st * CH + c) * 32 + lane) * SROW),
+                              text + ba[c] + (uint64_t)s * SLICE, sz[c], bar0 + 8 * st);
+            if (PF_SLICES > 0 && s % PF_SLICES == 0) {
+                // L2 prefetch of slices [s + STAGES, s + STAGES + PF_SLICES)
+#pragma unroll
+                for (int c = 0; c < CH; ++c) {
+                    const uint64_t p0 = ba[c] + (uint64_t)(s + STAGES) * SLICE;
+                    if (p0 < bb[c]) {
+                        const uint64_t p1 = p0 + (uint64_t)PF_SLICES * SLICE;
+                        bulk_prefetch_l2(text + p0, (uint32_t)((p1 < bb[c] ? p1 : bb[c]) - p0));
+                    }
+                }
+            }
+        };
+        for (uint32_t s = 0; s < (uint32_t)STAGES && s < nsl; ++s) issue(s);
+        for (uint32_t s = 0; s < nsl; ++s) {
+            const uint32_t st = s % STAGES;
+            wait_stage(bar0 + 8 * st, (parity >> st) & 1u, &S.hdr->err, S.timeout_us);
+            parity ^= 1u << st;
+            uint32_t len[CH];
+            bool allc = true;
 #pragma unroll
             for (int c = 0; c < CH; ++c) {
-                q[c] = ch[c].f;
-                cn[c] = ch[c].cnt;
+                const uint64_t off = ba[c] + (uint64_t)s * SLICE;
+                len[c] = s < nsl_c[c] ? (uint32_t)(bb[c] - off < (uint64_t)SLICE ? bb[c] - off : SLICE) : 0u;
+                allc &= constant(c) || len[c] == 0;
             }
-            if (m > 0) {
-                uint4 cur[CH];
+            if (allc) {
+                // fast path: every chunk of the thread is a constant mapping
+                // (a DFA state); one row lookup per byte, chunks interleaved
 #pragma unroll
-                for (int c = 0; c < CH; ++c) cur[c] = ldg128(text + pos[c]);
-                for (uint64_t it = 0; it < m; ++it) {
-                    uint4 nxt[CH];
-                    if (it + 1 < m) {
+                for (int g = 0; g < SLICE / 16; ++g) {
+                    uint4 v[CH];
 #pragma unroll
-                        for (int c = 0; c < CH; ++c) nxt[c] = ldg128(text + pos[c] + 16 * (it + 1));
+                    for (int c = 0; c < CH; ++c)
+                        v[c] = *reinterpret_cast<const uint4 *>(rows + ((size_t)(st * CH + c) * 32 + lane) * SROW + 16 * g);
+                    uint32_t q[CH], cn[CH];
+#pragma unroll
+                    for (int c = 0; c < CH; ++c) {
+                        q[c] = ch[c].f;
+                        cn[c] = ch[c].cnt;
                     }
 #pragma unroll
-                    for (int c = 0; c < CH; ++c) dfa_word(q[c], cn[c], cur[c].x, s_dfa, A);
+                    for (int c = 0; c < CH; ++c)
+                        if ((uint32_t)(16 * g) < len[c]) dfa_word(q[c], cn[c], v[c].x, s_dfa, A);
 #pragma unroll
-                    for (int c = 0; c < CH; ++c) dfa_word(q[c], cn[c], cur[c].y, s_dfa, A);
+                    for (int c = 0; c < CH; ++c)
+                        if ((uint32_t)(16 * g) < len[c]) dfa_word(q[c], cn[c], v[c].y, s_dfa, A);
 #pragma unroll
-                    for (int c = 0; c < CH; ++c) dfa_word(q[c], cn[c], cur[c].z, s_dfa, A);
+                    for (int c = 0; c < CH; ++c)
+                        if ((uint32_t)(16 * g) < len[c]) dfa_word(q[c], cn[c], v[c].z, s_dfa, A);
 #pragma unroll
-                    for (int c = 0; c < CH; ++c) dfa_word(q[c], cn[c], cur[c].w, s_dfa, A);
+                    for (int c = 0; c < CH; ++c)
+                        if ((uint32_t)(16 * g) < len[c]) dfa_word(q[c], cn[c], v[c].w, s_dfa, A);
 #pragma unroll
-                    for (int c = 0; c < CH; ++c) cur[c] = nxt[c];
+                    for (int c = 0; c < CH; ++c) {
+                        ch[c].f = q[c];
+                        ch[c].cnt = cn[c];
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int c = 0; c < CH; ++c) {
+                    const uint8_t *row = rows + ((size_t)(st * CH + c) * 32 + lane) * SROW;
+                    const int32_t j0 = (int32_t)(ba[c] + (uint64_t)s * SLICE - lo[c]);
+                    for (uint32_t g = 0; g < len[c]; g += 16) {
+                        const uint4 v = *reinterpret_cast<const uint4 *>(row + g);
+                        if (constant(c)) {
+                            uint32_t q = ch[c].f, cn = ch[c].cnt;
+                            dfa_word(q, cn, v.x, s_dfa, A);
+                            dfa_word(q, cn, v.y, s_dfa, A);
+                            dfa_word(q, cn, v.z, s_dfa, A);
+                            dfa_word(q, cn, v.w, s_dfa, A);
+                            ch[c].f = q;
+                            ch[c].cnt = cn;
+                        } else {
+                            const uint32_t ws[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                            for (int i = 0; i < 16; ++i)
+                                step(c, (ws[i >> 2] >> (8 * (i & 3))) & 0xffu, j0 + (int32_t)g + i);
+                        }
+                    }
                 }
             }
+            if (s + STAGES < nsl) issue(s + STAGES);
+        }
+
+        // tail bytes, then the chunk's mapping id
 #pragma unroll
-            for (int c = 0; c < CH; ++c) {
-                uint64_t p = pos[c] + 16 * m;
-                uint32_t qq = q[c], cc = cn[c];
-                for (; p + 16 <= hi[c]; p += 16) {
-                    const uint4 v = ldg128(text + p);
-                    dfa_word(qq, cc, v.x, s_dfa, A);
-                    dfa_word(qq, cc, v.y, s_dfa, A);
-                    dfa_word(qq, cc, v.z, s_dfa, A);
-                    dfa_word(qq, cc, v.w, s_dfa, A);
-                }
-                for (; p < hi[c]; ++p) {
-                    qq = s_dfa[(qq << 8) | text[p]];
-                    cc += qq >= A;
-                }
-                ch[c].f = qq;
-                ch[c].cnt = cc;
+        for (int c = 0; c < CH; ++c) {
+            for (uint64_t p = bb[c] > lo[c] ? bb[c] : lo[c]; p < hi[c]; ++p) step(c, text[p], (int32_t)(p - lo[c]));
+            if (SIMNQ && !con[c]) {
+                // keep the vector for the scan: id nr + global chunk index
+                const uint64_t gk = (uint64_t)gt * CPT + (uint64_t)c * THREADS + tid;
+                uint8_t *dst = S.chainvec + gk * nr;
+#pragma unroll
+                for (int i = 0; i < NQ / 4; ++i)
+#pragma unroll
+                    for (int b4 = 0; b4 < 4; ++b4)
+                        if ((uint32_t)(4 * i + b4) < nr) dst[4 * i + b4] = (V[c].w[i] >> (8 * b4)) & 0xffu;
+                ch[c].f = nr + (uint32_t)gk;
             }
         }
 
@@ -447,7 +550,7 @@ __global__ void __launch_bounds__(THREADS)
             uint64_t *st = S.status + gt;
             uint8_t *agg = S.agg + (size_t)gt * nr_max;
             const bool skip = (S.debug & SFA_DEBUG_SKIP_PUBLISH) && local == 1;
-            bool tconst = gconst != 0;
+            const bool tconst = gconst != 0;
             uint32_t tval = 0;
             if (tconst) {
                 const int gc = 31 - __clz(gconst);
@@ -455,8 +558,8 @@ __global__ void __launch_bounds__(THREADS)
                 for (int g = gc + 1; g < G; ++g) tval = s_gvec[(size_t)g * nr + tval];
                 if (lane == 0 && !skip) st_release(st, ST_PREFIX | tval);
             } else {
-                for (uint32_t q0 = 0; q0 < nr; q0 += 32) {
-                    const uint32_t q = q0 + lane;
+                for (uint32_t qb = 0; qb < nr; qb += 32) {
+                    const uint32_t q = qb + lane;
                     if (q < nr) {
                         uint32_t v = q;
                         for (int g = 0; g < G; ++g) v = s_gvec[(size_t)g * nr + v];

@@ -77,6 +77,31 @@ SFA_HD inline uint64_t num_chunks(const TextDesc &d) {
 // ---------------------------------------------------------------------------
 // shared memory of one CTA
 // ---------------------------------------------------------------------------
+// DFA rows in shared memory are ROWB = 260 bytes apart: byte b of state q sits
+// in bank (q + b/4) mod 32, so lanes reading the same byte value in different
+// states hit different banks (a 256-byte stride would put them all in one).
+constexpr uint32_t ROWB = 260;
+// text staging: bulk copies of SLICE bytes per chunk, STAGES in flight; rows
+// are SROW bytes apart so that 16-byte reads of 8 consecutive lanes hit
+// distinct banks
+// Every PF_SLICES slices a chunk also asks L2 to prefetch the PF_SLICES
+// slices after the ones in flight, so that the staging copies hit L2.
+#ifndef SFA_SLICE
+#define SFA_SLICE 64
+#endif
+#ifndef SFA_STAGES
+#define SFA_STAGES 2
+#endif
+#ifndef SFA_PF_SLICES
+#define SFA_PF_SLICES 4
+#endif
+constexpr int SLICE = SFA_SLICE;
+constexpr int STAGES = SFA_STAGES;
+constexpr int SROW = SLICE + 16;
+constexpr int PF_SLICES = SFA_PF_SLICES;
+static_assert(SLICE % 16 == 0, "slice of whole 16-byte words");
+static_assert((SROW / 16) % 2 == 1, "row stride an odd number of 16-byte words");
+
 template <int THREADS, int CH>
 struct SmemLayout {
     static constexpr int CPT = THREADS * CH;   // chunks per tile
@@ -84,15 +109,20 @@ struct SmemLayout {
     static constexpr int G = CPT / 32;         // groups per tile
     static_assert(G <= 32, "at most 1024 chunks per tile");
     // offsets in bytes from the start of dynamic shared memory
+    static SFA_HD size_t a16(size_t x) { return (x + 15) & ~(size_t)15; }
     static SFA_HD size_t dfa_off() { return 0; }
-    static SFA_HD size_t cls_off(uint32_t nr_max) { return (size_t)nr_max * 256; }
+    static SFA_HD size_t cls_off(uint32_t nr_max) { return a16((size_t)nr_max * ROWB); }
     static SFA_HD size_t f_off(uint32_t nr_max) { return cls_off(nr_max) + 256; }
     static SFA_HD size_t gval_off(uint32_t nr_max) { return f_off(nr_max) + CPT * 4; }
     static SFA_HD size_t gpre_off(uint32_t nr_max) { return gval_off(nr_max) + 32 * 4; }
     static SFA_HD size_t misc_off(uint32_t nr_max) { return gpre_off(nr_max) + 32 * 4; }
-    static SFA_HD size_t gvec_off(uint32_t nr_max) { return misc_off(nr_max) + 256; }
+    static SFA_HD size_t gvec_off(uint32_t nr_max) { return misc_off(nr_max) + 512; }
+    static SFA_HD size_t bar_off(uint32_t nr_max) { return a16(gvec_off(nr_max) + (size_t)G * nr_max); }
+    static SFA_HD size_t stage_off(uint32_t nr_max) {
+        return (bar_off(nr_max) + (size_t)NW * STAGES * 8 + 127) & ~(size_t)127;
+    }
     static SFA_HD size_t bytes(uint32_t nr_max) {
-        return (gvec_off(nr_max) + (size_t)G * nr_max + 15) & ~(size_t)15;
+        return stage_off(nr_max) + (size_t)NW * STAGES * CH * 32 * SROW;
     }
 };
 
@@ -102,8 +132,8 @@ struct Misc {
     uint32_t s_in;          // entering state of the tile
     uint32_t incl;          // state after the tile
     uint32_t pad[4];
-    unsigned long long wsum[16];
+    unsigned long long wsum[32];
 };
-static_assert(sizeof(Misc) <= 256, "misc region");
+static_assert(sizeof(Misc) <= 512, "misc region");
 
 }  // namespace sfa_dev

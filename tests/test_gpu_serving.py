@@ -1,0 +1,114 @@
+"""Continuous batching: reserved batch plans refilled with sfa_batch_update,
+and the Server loop.  Every result must equal the text's result alone and
+the oracle's (integers, tolerance 0)."""
+import ctypes
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def sfa():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    import paper_1405_0562_gb300 as m
+    m.lib()
+    torch.cuda.set_device(0)
+    return m
+
+
+def expect(d, t):
+    f, acc, c = oracle.dfa_run(d.delta, d.q0, d.accept, t)
+    return (f, acc, 0, c)
+
+
+def test_reserved_plan_refilled(sfa):
+    autos_d = W.workload_serving_automata(6)
+    autos = [sfa.Automaton.from_dfa(d) for d in autos_d]
+    nr_max = max(a.info()["n_reachable"] for a in autos)
+    L = sfa.lib()
+    opts = sfa.LaunchOpts(512, 256, 2, 0, 0, 0, 0, 0)
+    plan = ctypes.c_void_p()
+    assert L.sfa_batch_reserve(64, 4096, nr_max, ctypes.byref(opts), ctypes.byref(plan)) == sfa.OK
+    stream = torch.cuda.Stream()
+    rng = np.random.default_rng(1)
+    try:
+        for rnd in range(5):
+            k = int(rng.integers(1, 40))
+            lens = [int(x) for x in rng.integers(0, 300_000, k)]
+            which = [int(x) for x in rng.integers(0, len(autos), k)]
+            texts = [W.text_uniform(n, W.LOWER_ALPHABET, 100 * rnd + i) for i, n in enumerate(lens)]
+            dev = [torch.from_numpy(t).cuda() for t in texts]
+            hs = (ctypes.c_void_p * k)(*[autos[j].handle.value for j in which])
+            ptrs = (ctypes.c_void_p * k)(*[x.data_ptr() if x.numel() else 0 for x in dev])
+            ln = (ctypes.c_uint64 * k)(*lens)
+            out = torch.zeros(16 * 64, dtype=torch.uint8, device="cuda")
+            torch.cuda.synchronize()
+            assert L.sfa_batch_update(plan, hs, ptrs, ln, k, stream.cuda_stream) == sfa.OK
+            fn = L.sfa_batch_graph_launch if rnd % 2 else L.sfa_batch_launch
+            assert fn(plan, out.data_ptr(), stream.cuda_stream) == sfa.OK
+            stream.synchronize()
+            got = sfa.decode(out[:16 * k])
+            assert got == [expect(autos_d[j], t) for j, t in zip(which, texts)], rnd
+    finally:
+        L.sfa_batch_destroy(plan)
+
+
+def test_reserved_plan_refuses_over_capacity(sfa):
+    """A real text that needs more tiles than the plan holds is refused by
+    sfa_batch_update (nothing is launched)."""
+    d = W.workload_serving_automata(1)[0]
+    a = sfa.Automaton.from_dfa(d)
+    L = sfa.lib()
+    opts = sfa.LaunchOpts(512, 256, 2, 0, 0, 0, 0, 0)
+    plan = ctypes.c_void_p()
+    assert L.sfa_batch_reserve(4, 2, a.info()["n_reachable"], ctypes.byref(opts), ctypes.byref(plan)) == sfa.OK
+    stream = torch.cuda.Stream()
+    try:
+        t = torch.from_numpy(W.text_uniform(4 << 20, W.LOWER_ALPHABET, 3)).cuda()   # 16 tiles of 256 KiB
+        hs = (ctypes.c_void_p * 1)(a.handle.value)
+        ptrs = (ctypes.c_void_p * 1)(t.data_ptr())
+        ln = (ctypes.c_uint64 * 1)(t.numel())
+        assert L.sfa_batch_update(plan, hs, ptrs, ln, 1, stream.cuda_stream) == sfa.ERR_INVALID
+        five = (ctypes.c_void_p * 5)(*([a.handle.value] * 5))
+        p5 = (ctypes.c_void_p * 5)(*([t.data_ptr()] * 5))
+        l5 = (ctypes.c_uint64 * 5)(*([16] * 5))
+        assert L.sfa_batch_update(plan, five, p5, l5, 5, stream.cuda_stream) == sfa.ERR_INVALID   # > 4 texts
+        stream.synchronize()
+    finally:
+        L.sfa_batch_destroy(plan)
+
+
+def test_server_results_equal_alone(sfa):
+    from paper_1405_0562_gb300 import serve
+    autos_d = W.workload_serving_automata(8)
+    autos = [sfa.Automaton.from_dfa(d) for d in autos_d]
+    arrivals, lens, which = W.workload_serving_requests(300, rate_per_s=20000.0, n_automata=len(autos),
+                                                       median=16 << 10, cap=2 << 20)
+    reqs = []
+    for i in range(len(lens)):
+        t = W.text_uniform(int(lens[i]), W.LOWER_ALPHABET, 7000 + i)
+        reqs.append(serve.Request(i, int(which[i]), torch.from_numpy(t).pin_memory(), float(arrivals[i])))
+    srv = serve.Server(autos, hbm_budget=64 << 20, max_batch=64, slots=3)
+    try:
+        done = srv.run(reqs)
+    finally:
+        srv.close()
+    assert len(done) == len(reqs)
+    assert srv.batches < len(reqs)          # requests were batched
+    for r in done:
+        t = r.text.numpy()
+        assert r.result == expect(autos_d[r.automaton], t), r.rid
+    # one request at a time gives the same results
+    alone = serve.one_at_a_time(autos, [serve.Request(r.rid, r.automaton, r.text, 0.0) for r in done[:40]],
+                                realtime=False)
+    by_id = {r.rid: r.result for r in done}
+    for r in alone:
+        assert r.result == by_id[r.rid]

@@ -220,3 +220,21 @@ def test_class_compression_is_exact():
     # and different classes differ somewhere
     reps = [int(np.nonzero(cls == c)[0][0]) for c in np.unique(cls)]
     assert len({tuple(d.delta[:, b]) for b in reps}) == len(reps)
+
+
+def test_noalloc_refusals_need_no_device():
+    """sfa_match_noalloc decides every refusal on the host, before it touches
+    a device: checked here with host-only handles (no GPU in this process)."""
+    L = sfa.lib()
+    L.sfa_match_noalloc.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p,
+                                    ctypes.c_void_p]
+    big = host(W.workload_large(1 << 12)[0])              # 127 states: ~135 B of scratch per tile
+    fake = ctypes.c_void_p(1 << 20)                        # never dereferenced
+    assert L.sfa_match_noalloc(big.handle, fake, 1 << 40, fake, None) == sfa.ERR_SCRATCH_LIMIT
+    assert L.sfa_match_noalloc(big.handle, None, 16, fake, None) == sfa.ERR_INVALID
+    assert L.sfa_match_noalloc(big.handle, fake, 16, None, None) == sfa.ERR_INVALID
+    sim = host(W.workload_sim_automata()[0])
+    assert L.sfa_match_noalloc(sim.handle, fake, 16, fake, None) == sfa.ERR_UNSUPPORTED
+    # a text that fits passes the host checks and then needs a device (and the
+    # handle's device tables)
+    assert L.sfa_match_noalloc(big.handle, fake, 1 << 20, fake, None) in (sfa.ERR_NO_DEVICE, sfa.ERR_HOST_ONLY)
