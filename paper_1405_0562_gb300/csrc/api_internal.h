@@ -2,6 +2,7 @@
 // noalloc.cu): the handle, launch shapes, scratch plans, launch helpers.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <atomic>
@@ -94,9 +95,14 @@ namespace sfa_impl {
 int choose_shape(const sfa_handle *h, uint64_t n, const sfa_launch_opts *o, Shape &sh);
 // grow the handle's scratch to at least `bytes` (may synchronise and cudaMalloc)
 int ensure_scratch(sfa_handle *h, size_t bytes);
-// enqueue one persistent kernel on `s`
+// If the text can be staged by 2-D tensor copies (16-byte-aligned text,
+// chunks of a multiple of 16 bytes, not a forced chunk count), encode the
+// tensor map of its full chunks and set d.rows2d; else leave d.rows2d = 0.
+void fill_text_map(sfa_dev::TextDesc &d, CUtensorMap &map);
+// enqueue one persistent kernel on `s` (tmap: the text's tensor map, or NULL)
 int launch_kernel(const void *k, int threads, size_t smem, uint32_t tiles, int max_ctas, cudaStream_t s,
-                  const sfa_dev::Tables &tab, const sfa_dev::TextDesc &desc, const sfa_dev::Tables *tabs,
+                  const sfa_dev::Tables &tab, const sfa_dev::TextDesc &desc, const CUtensorMap *tmap,
+                  const sfa_dev::Tables *tabs,
                   const sfa_dev::TextDesc *descs, const uint32_t *tile_text, const sfa_dev::Scratch &S,
                   sfa_result *out);
 // one text (sfa_match_ex / sfa_match_continue)

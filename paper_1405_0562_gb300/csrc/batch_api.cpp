@@ -175,7 +175,7 @@ int batch_enqueue(sfa_batch *b, sfa_result *d_out, cudaStream_t s) {
         // the device, so the launch does not depend on the work list
         const uint32_t grid_tiles = b->reserved ? 0xffffffffu : b->total_tiles;
         int rc = launch_kernel(b->kernel, b->shape.threads, b->smem, grid_tiles, b->shape.max_ctas, s, Tables{},
-                               TextDesc{}, reinterpret_cast<const Tables *>(b->d_mem + b->off_tabs),
+                               TextDesc{}, nullptr, reinterpret_cast<const Tables *>(b->d_mem + b->off_tabs),
                                reinterpret_cast<const TextDesc *>(b->d_mem + b->off_descs),
                                reinterpret_cast<const uint32_t *>(b->d_mem + b->off_tt), b->S, d_out);
         if (rc) return rc;

@@ -184,9 +184,40 @@ int ensure_scratch(sfa_handle *h, size_t bytes) {
     return SFA_OK;
 }
 
+void fill_text_map(TextDesc &d, CUtensorMap &map) {
+    using EncodeFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+    static EncodeFn encode = [] {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            fn = nullptr;
+        return reinterpret_cast<EncodeFn>(fn);
+    }();
+    d.rows2d = 0;
+    std::memset(&map, 0, sizeof map);
+    const uint64_t rows = d.chunk ? d.n / d.chunk : 0;
+    if (!encode || d.forced || d.chunk % 16 || d.chunk > 0xffffffffull ||
+        (reinterpret_cast<uintptr_t>(d.text) & 15) || rows == 0 || rows >= (1ull << 31))
+        return;
+    // the text's full chunks as a [rows][chunk] byte matrix; boxes of
+    // 32 chunks x SLICE bytes, 64-byte swizzled in shared memory
+    const cuuint64_t dims[2] = {d.chunk, rows};
+    const cuuint64_t strides[1] = {d.chunk};
+    const cuuint32_t box[2] = {(cuuint32_t)sfa_dev::SLICE, 32};
+    const cuuint32_t estr[2] = {1, 1};
+    if (encode(&map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<uint8_t *>(d.text), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS)
+        d.rows2d = (uint32_t)rows;
+}
+
 int launch_kernel(const void *k, int threads, size_t smem, uint32_t tiles, int max_ctas, cudaStream_t s,
-                  const Tables &tab, const TextDesc &desc, const Tables *tabs, const TextDesc *descs,
-                  const uint32_t *tile_text, const Scratch &S, sfa_result *out) {
+                  const Tables &tab, const TextDesc &desc, const CUtensorMap *tmap, const Tables *tabs,
+                  const TextDesc *descs, const uint32_t *tile_text, const Scratch &S, sfa_result *out) {
     const int bps = blocks_per_sm(k, threads, smem);
     if (bps < 1) return SFA_ERR_UNSUPPORTED;
     int dev = 0;
@@ -196,12 +227,17 @@ int launch_kernel(const void *k, int threads, size_t smem, uint32_t tiles, int m
     grid = std::max<uint64_t>(1, std::min<uint64_t>(grid, tiles));
     Tables a0 = tab;
     TextDesc a1 = desc;
-    const Tables *a2 = tabs;
-    const TextDesc *a3 = descs;
-    const uint32_t *a4 = tile_text;
-    Scratch a5 = S;
-    sfa_result *a6 = out;
-    void *args[] = {&a0, &a1, &a2, &a3, &a4, &a5, &a6};
+    alignas(64) CUtensorMap a2;
+    if (tmap)
+        a2 = *tmap;
+    else
+        std::memset(&a2, 0, sizeof a2);
+    const Tables *a3 = tabs;
+    const TextDesc *a4 = descs;
+    const uint32_t *a5 = tile_text;
+    Scratch a6 = S;
+    sfa_result *a7 = out;
+    void *args[] = {&a0, &a1, &a2, &a3, &a4, &a5, &a6, &a7};
     CK(cudaLaunchKernel(k, dim3((unsigned)grid), dim3(threads), args, smem, s));
     g_launches.fetch_add(1, std::memory_order_relaxed);
     return SFA_OK;
@@ -238,7 +274,9 @@ int match_impl(sfa_handle *h, const uint8_t *d_text, uint64_t n, sfa_result *d_o
     Scratch S = make_scratch(h->d_scratch, p, nr, (uint32_t)tiles, sh);
     const void *k = sfa_impl::kernel_for(sh.threads, sh.chains, sh.simnq, false);
     const size_t smem = sfa_impl::smem_bytes(sh.threads, sh.chains, nr);
-    return launch_kernel(k, sh.threads, smem, (uint32_t)tiles, sh.max_ctas, s, h->dev, d, nullptr, nullptr,
+    alignas(64) CUtensorMap map;
+    fill_text_map(d, map);
+    return launch_kernel(k, sh.threads, smem, (uint32_t)tiles, sh.max_ctas, s, h->dev, d, &map, nullptr, nullptr,
                          nullptr, S, d_out);
 }
 
@@ -479,7 +517,9 @@ int match_into_scratch(sfa_handle_t h, const uint8_t *d_text, uint64_t n, sfa_re
     const Scratch S = make_scratch(scratch, p, nr, (uint32_t)tiles, sh);
     const void *k = kernel_for(sh.threads, sh.chains, 0, false);
     const size_t smem = smem_bytes(sh.threads, sh.chains, nr);
-    return launch_kernel(k, sh.threads, smem, (uint32_t)tiles, 0, s, h->dev, d, nullptr, nullptr, nullptr, S,
+    alignas(64) CUtensorMap map;
+    fill_text_map(d, map);
+    return launch_kernel(k, sh.threads, smem, (uint32_t)tiles, 0, s, h->dev, d, &map, nullptr, nullptr, nullptr, S,
                          d_out);
 }
 

@@ -11,8 +11,10 @@
 //   group    32 consecutive chunks of a tile (one warp, one round)
 //
 // Text staging: a chunk's 16-byte-aligned body arrives in shared memory by
-// bulk asynchronous copies (cp.async.bulk, completed on one mbarrier per warp
-// and stage), SLICE bytes per copy and STAGES copies in flight; the unaligned
+// asynchronous copies completed on one mbarrier per warp and stage, SLICE
+// bytes per chunk per step and STAGES steps in flight: one 2-D tensor copy per
+// warp moves the slice of its 32 chunks at once (the text seen as rows of the
+// chunk length); chunks that are not full rows use 1-D bulk copies; unaligned
 // head and tail bytes are read singly.  The copies bypass the load/store data
 // path, which the table lookups need for themselves.
 //
@@ -25,6 +27,8 @@
 // over the prefix up to that position.  For synchronising automata (all
 // literal automata) that prefix is at most the longest literal.
 #pragma once
+
+#include <cuda.h>
 
 #include <cstdint>
 
@@ -83,9 +87,14 @@ __device__ __forceinline__ void bulk_copy(uint32_t dst, const uint8_t *src, uint
         "l"(src), "r"(bytes), "r"(bar)
         : "memory");
 }
-// hint: bring [src, src + bytes) into L2 (16-byte aligned, multiple of 16)
-__device__ __forceinline__ void bulk_prefetch_l2(const uint8_t *src, uint32_t bytes) {
-    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+// 2-D tensor copy of the box at (x, y) of `map` into shared memory, completing
+// its bytes (the whole box, out-of-range elements included) on the mbarrier
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+        "[%4];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+        : "memory");
 }
 __device__ __forceinline__ void fence_proxy_async_smem() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -173,29 +182,35 @@ __device__ __forceinline__ void dfa_word(uint32_t &q, uint32_t &cnt, uint32_t w,
 }
 
 // ---------------------------------------------------------------------------
-// simulation mode: the |Q|-vector T[q] of Alg. 3, packed four states per word
+// simulation mode: the |Q|-vector T[q] of Alg. 3.  While T has many distinct
+// entries it is kept whole, four states per register (SIM_FULL).  Once at
+// most 8 distinct values are left it is kept as those values U[0..7] and, for
+// each q, the slot of T[q] among them (SIM_COMPACT): a byte then costs 8
+// lookups instead of NQ.  With one value left T is constant (SIM_CONST) and
+// the chunk runs on the DFA rows.  The representation is re-examined every
+// 16 bytes; the vector it stands for is the same in every form.
 // ---------------------------------------------------------------------------
-template <int NQ>
-struct SimVec {
-    uint32_t w[NQ / 4];
-};
+enum : uint32_t { SIM_FULL = 0, SIM_COMPACT = 1, SIM_CONST = 2 };
 
 template <int NQ>
-__device__ __forceinline__ void sim_step(SimVec<NQ> &T, Chain &s, uint32_t b, int32_t j,
-                                         const uint8_t *s_dfa, uint32_t first_accept) {
-    uint32_t mn = 0xffffffffu, mx = 0;
-#pragma unroll
-    for (int i = 0; i < NQ / 4; ++i) {
-        const uint32_t x = T.w[i];
-        const uint32_t y0 = s_dfa[__byte_perm(x, 0, 0x4440) * ROWB + b];
-        const uint32_t y1 = s_dfa[__byte_perm(x, 0, 0x4441) * ROWB + b];
-        const uint32_t y2 = s_dfa[__byte_perm(x, 0, 0x4442) * ROWB + b];
-        const uint32_t y3 = s_dfa[__byte_perm(x, 0, 0x4443) * ROWB + b];
-        const uint32_t y = __byte_perm(__byte_perm(y0, y1, 0x0040), __byte_perm(y2, y3, 0x0040), 0x5410);
-        T.w[i] = y;
-        mn = __vminu4(mn, y);
-        mx = __vmaxu4(mx, y);
-    }
+struct SimChain {
+    uint32_t w[NQ / 4];   // SIM_FULL: T[q]; SIM_COMPACT: slot of T[q]
+    uint32_t u0, u1;      // SIM_COMPACT: U[0..7] (slots past d repeat U[0])
+    uint32_t d;           // SIM_COMPACT: number of distinct values
+    uint32_t mode;
+};
+
+// the successors of four packed states on byte b, packed
+__device__ __forceinline__ uint32_t step4(uint32_t x, uint32_t b, const uint8_t *s_dfa) {
+    const uint32_t y0 = s_dfa[__byte_perm(x, 0, 0x4440) * ROWB + b];
+    const uint32_t y1 = s_dfa[__byte_perm(x, 0, 0x4441) * ROWB + b];
+    const uint32_t y2 = s_dfa[__byte_perm(x, 0, 0x4442) * ROWB + b];
+    const uint32_t y3 = s_dfa[__byte_perm(x, 0, 0x4443) * ROWB + b];
+    return __byte_perm(__byte_perm(y0, y1, 0x0040), __byte_perm(y2, y3, 0x0040), 0x5410);
+}
+
+// final for all, some or none of the entries, from packed minima and maxima
+__device__ __forceinline__ void acc_update(Chain &s, uint32_t mn, uint32_t mx, int32_t j, uint32_t first_accept) {
     mn = __vminu4(mn, mn >> 16);
     mn = __vminu4(mn, mn >> 8) & 0xffu;
     mx = __vmaxu4(mx, mx >> 16);
@@ -209,12 +224,109 @@ __device__ __forceinline__ void sim_step(SimVec<NQ> &T, Chain &s, uint32_t b, in
 }
 
 template <int NQ>
-__device__ __forceinline__ bool sim_constant(const SimVec<NQ> &T) {
-    const uint32_t splat = (T.w[0] & 0xffu) * 0x01010101u;
-    bool c = true;
+__device__ __forceinline__ void sim_byte(SimChain<NQ> &T, Chain &s, uint32_t b, int32_t j, const uint8_t *s_dfa,
+                                         uint32_t first_accept) {
+    if (T.mode == SIM_CONST) {
+        s.f = s_dfa[didx(s.f, b)];
+        s.cnt += s.f >= first_accept;
+        return;
+    }
+    uint32_t mn, mx;
+    if (T.mode == SIM_FULL) {
+        mn = 0xffffffffu;
+        mx = 0;
 #pragma unroll
-    for (int i = 0; i < NQ / 4; ++i) c &= T.w[i] == splat;
-    return c;
+        for (int i = 0; i < NQ / 4; ++i) {
+            const uint32_t y = step4(T.w[i], b, s_dfa);
+            T.w[i] = y;
+            mn = __vminu4(mn, y);
+            mx = __vmaxu4(mx, y);
+        }
+    } else {
+        T.u0 = step4(T.u0, b, s_dfa);
+        T.u1 = step4(T.u1, b, s_dfa);
+        mn = __vminu4(T.u0, T.u1);
+        mx = __vmaxu4(T.u0, T.u1);
+    }
+    acc_update(s, mn, mx, j, first_accept);
+}
+
+__device__ __forceinline__ uint32_t rank64(uint64_t m, uint32_t v) {
+    return (uint32_t)__popcll(m & ((1ull << v) - 1ull));
+}
+// the (at most 8) values of a mask in ascending order, padded with the first
+__device__ __forceinline__ void mask_values(uint64_t m, uint32_t &u0, uint32_t &u1) {
+    const uint32_t first = (uint32_t)__ffsll((long long)m) - 1u;
+    uint32_t v[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        if (m) {
+            v[k] = (uint32_t)__ffsll((long long)m) - 1u;
+            m &= m - 1ull;
+        } else {
+            v[k] = first;
+        }
+    }
+    u0 = v[0] | (v[1] << 8) | (v[2] << 16) | (v[3] << 24);
+    u1 = v[4] | (v[5] << 8) | (v[6] << 16) | (v[7] << 24);
+}
+// selector of __byte_perm that picks U[slot] for the four slots of a word
+__device__ __forceinline__ uint32_t slots_sel(uint32_t x) {
+    return (x & 0x7u) | ((x >> 4) & 0x70u) | ((x >> 8) & 0x700u) | ((x >> 12) & 0x7000u);
+}
+
+// re-examine the representation (every 16 bytes); kept states are < 64
+template <int NQ>
+__device__ __forceinline__ void sim_compact(SimChain<NQ> &T, Chain &s) {
+    if (T.mode == SIM_FULL) {
+        uint64_t m = 0;
+#pragma unroll
+        for (int i = 0; i < NQ / 4; ++i)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) m |= 1ull << ((T.w[i] >> (8 * k)) & 0xffu);
+        const int dd = __popcll(m);
+        if (dd == 1) {
+            T.mode = SIM_CONST;
+            s.f = (uint32_t)__ffsll((long long)m) - 1u;
+            return;
+        }
+        if (dd > 8) return;
+#pragma unroll
+        for (int i = 0; i < NQ / 4; ++i) {
+            const uint32_t x = T.w[i];
+            T.w[i] = rank64(m, x & 0xffu) | (rank64(m, (x >> 8) & 0xffu) << 8) |
+                     (rank64(m, (x >> 16) & 0xffu) << 16) | (rank64(m, x >> 24) << 24);
+        }
+        mask_values(m, T.u0, T.u1);
+        T.d = (uint32_t)dd;
+        T.mode = SIM_COMPACT;
+    } else if (T.mode == SIM_COMPACT) {
+        uint64_t m = 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) m |= (1ull << ((T.u0 >> (8 * k)) & 0xffu)) | (1ull << ((T.u1 >> (8 * k)) & 0xffu));
+        const int dd = __popcll(m);
+        if (dd == 1) {
+            T.mode = SIM_CONST;
+            s.f = T.u0 & 0xffu;
+            return;
+        }
+        if ((uint32_t)dd == T.d) return;
+        // old slot k moves to the rank of U[k] among the values left
+        const uint32_t n0 = rank64(m, T.u0 & 0xffu) | (rank64(m, (T.u0 >> 8) & 0xffu) << 8) |
+                            (rank64(m, (T.u0 >> 16) & 0xffu) << 16) | (rank64(m, T.u0 >> 24) << 24);
+        const uint32_t n1 = rank64(m, T.u1 & 0xffu) | (rank64(m, (T.u1 >> 8) & 0xffu) << 8) |
+                            (rank64(m, (T.u1 >> 16) & 0xffu) << 16) | (rank64(m, T.u1 >> 24) << 24);
+#pragma unroll
+        for (int i = 0; i < NQ / 4; ++i) T.w[i] = __byte_perm(n0, n1, slots_sel(T.w[i]));
+        mask_values(m, T.u0, T.u1);
+        T.d = (uint32_t)dd;
+    }
+}
+
+// the four entries T[4i..4i+3] of a non-constant chain
+template <int NQ>
+__device__ __forceinline__ uint32_t sim_word(const SimChain<NQ> &T, int i) {
+    return T.mode == SIM_FULL ? T.w[i] : __byte_perm(T.u0, T.u1, slots_sel(T.w[i]));
 }
 
 // mapping applied to a state: constant ids are their own value
@@ -253,7 +365,8 @@ __device__ __forceinline__ uint32_t dfa_count(const uint8_t *text, uint64_t p, u
 // ---------------------------------------------------------------------------
 template <int THREADS, int CH, int SIMNQ, bool BATCH>
 __global__ void __launch_bounds__(THREADS)
-    sfa_match_kernel(Tables tab, TextDesc desc, const Tables *tabs, const TextDesc *descs,
+    sfa_match_kernel(Tables tab, TextDesc desc, const __grid_constant__ CUtensorMap tmap, const Tables *tabs,
+                     const TextDesc *descs,
                      const uint32_t *tile_text, Scratch S, sfa_result *out) {
     using L = SmemLayout<THREADS, CH>;
     constexpr int CPT = L::CPT, NW = L::NW, G = L::G;
@@ -270,9 +383,10 @@ __global__ void __launch_bounds__(THREADS)
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t lanemask_lt = (1u << lane) - 1u;
-    // this warp's stage barriers and this lane's staging rows
+    // this warp's stage barriers and staging buffers
     const uint32_t bar0 = smem_addr(smem + L::bar_off(nr_max)) + (uint32_t)warp * STAGES * 8;
-    uint8_t *rows = smem + L::stage_off(nr_max) + (size_t)warp * STAGES * CH * 32 * SROW;
+    uint8_t *s_box = smem + L::stage_off(nr_max) + (size_t)warp * STAGES * CH * BOX;
+    uint8_t *s_extra = smem + L::extra_off(nr_max) + (size_t)warp * STAGES * CH * SLICE;
     if (lane == 0)
         for (int s = 0; s < STAGES; ++s) mbar_init(bar0 + 8 * s, 1);
     mbar_init_fence();
@@ -316,8 +430,7 @@ __global__ void __launch_bounds__(THREADS)
 
         // ---------------- pass 1: every chunk from f_I ----------------
         Chain ch[CH];
-        SimVec<NQ> V[CH];
-        bool con[CH];                // simulation: the vector is constant
+        SimChain<NQ> V[CH];          // simulation: the chunk's vector T
         uint64_t lo[CH], hi[CH], ba[CH], bb[CH];
 #pragma unroll
         for (int c = 0; c < CH; ++c) {
@@ -340,8 +453,8 @@ __global__ void __launch_bounds__(THREADS)
             ch[c].cnt = 0;
             ch[c].snap = 0;
             ch[c].lm = -1;
-            con[c] = nr == 1;
             if (SIMNQ) {
+                // T = f_I over the kept states; padding entries follow state 0
 #pragma unroll
                 for (int i = 0; i < NQ / 4; ++i) {
                     uint32_t w = 0;
@@ -352,26 +465,21 @@ __global__ void __launch_bounds__(THREADS)
                     }
                     V[c].w[i] = w;
                 }
-                if (con[c]) ch[c].f = 0;
+                V[c].u0 = V[c].u1 = 0;
+                V[c].d = 0;
+                V[c].mode = nr == 1 ? SIM_CONST : SIM_FULL;
+                if (nr == 1) ch[c].f = 0;
             }
         }
 
         // one symbol of either mode
         auto step = [&](int c, uint32_t b, int32_t j) {
-            if (SIMNQ) {
-                if (!con[c]) {
-                    sim_step<NQ>(V[c], ch[c], b, j, s_dfa, A);
-                    con[c] = sim_constant<NQ>(V[c]);
-                    if (con[c]) ch[c].f = V[c].w[0] & 0xffu;
-                } else {
-                    ch[c].f = s_dfa[didx(ch[c].f, b)];
-                    ch[c].cnt += ch[c].f >= A;
-                }
-            } else {
+            if (SIMNQ)
+                sim_byte<NQ>(V[c], ch[c], b, j, s_dfa, A);
+            else
                 sfa_step(ch[c], b, j, s_dfa, s_cls, T.nc, nr, T.ncls, A);
-            }
         };
-        auto constant = [&](int c) -> bool { return SIMNQ ? con[c] : ch[c].f < nr; };
+        auto constant = [&](int c) -> bool { return SIMNQ ? V[c].mode == SIM_CONST : ch[c].f < nr; };
 
         // head bytes
 #pragma unroll
@@ -379,42 +487,56 @@ __global__ void __launch_bounds__(THREADS)
             for (uint64_t p = lo[c]; p < ba[c]; ++p) step(c, text[p], (int32_t)(p - lo[c]));
 
         // body: slices through shared memory
-        uint32_t nsl_c[CH];
+        bool reg2d[CH];          // this lane's chunk is a row of the tensor map
+        uint32_t nsl_c[CH], boxw = 0;
         uint32_t nsl = 0;
 #pragma unroll
         for (int c = 0; c < CH; ++c) {
+            const uint64_t k = (uint64_t)local * CPT + (uint64_t)c * THREADS + tid;
+            reg2d[c] = k < d.rows2d;
+            if (__ballot_sync(0xffffffffu, reg2d[c])) boxw |= 1u << c;
             nsl_c[c] = (uint32_t)((bb[c] - ba[c] + SLICE - 1) / SLICE);
             nsl = nsl_c[c] > nsl ? nsl_c[c] : nsl;
         }
         nsl = __reduce_max_sync(0xffffffffu, nsl);
+        const uint32_t nsl_box = (uint32_t)((d.chunk + SLICE - 1) / SLICE);
+        // staging addresses: box of (stage, round), this lane's 1-D row, and
+        // the 16-byte unit g of this lane's slice
+        auto box_at = [&](uint32_t st, int c) -> uint8_t * {
+            return s_box + ((size_t)(st * CH + c)) * BOX;
+        };
+        auto row1d = [&](uint32_t st, int c) -> uint8_t * {
+            return d.rows2d ? s_extra + (size_t)(st * CH + c) * SLICE : box_at(st, c) + lane * SLICE;
+        };
+        auto unit = [&](uint32_t st, int c, uint32_t g) -> const uint4 * {
+            const uint8_t *p = reg2d[c] ? box_at(st, c) + lane * SLICE + ((g ^ ((uint32_t)(lane >> 1) & 3u)) << 4)
+                                        : row1d(st, c) + (g << 4);
+            return reinterpret_cast<const uint4 *>(p);
+        };
         auto issue = [&](uint32_t s) {
             const uint32_t st = s % STAGES;
             uint32_t sz[CH], tot = 0;
 #pragma unroll
             for (int c = 0; c < CH; ++c) {
                 const uint64_t off = ba[c] + (uint64_t)s * SLICE;
-                sz[c] = s < nsl_c[c] ? (uint32_t)(bb[c] - off < (uint64_t)SLICE ? bb[c] - off : SLICE) : 0u;
+                sz[c] = !reg2d[c] && s < nsl_c[c] ? (uint32_t)(bb[c] - off < (uint64_t)SLICE ? bb[c] - off : SLICE) : 0u;
                 tot += sz[c];
             }
             tot = __reduce_add_sync(0xffffffffu, tot);
+            const bool boxes = s < nsl_box;
+#pragma unroll
+            for (int c = 0; c < CH; ++c)
+                if (boxes && (boxw >> c) & 1u) tot += BOX;
             if (lane == 0) mbar_arrive_expect_tx(bar0 + 8 * st, tot);
             __syncwarp();
             fence_proxy_async_smem();
 #pragma unroll
-            for (int c = 0; c < CH; ++c)
-                if (sz[c])
-                    bulk_copy(smem_addr(rows + ((size_t)(st * CH + c) * 32 + lane) * SROW),
-                              text + ba[c] + (uint64_t)s * SLICE, sz[c], bar0 + 8 * st);
-            if (PF_SLICES > 0 && s % PF_SLICES == 0) {
-                // L2 prefetch of slices [s + STAGES, s + STAGES + PF_SLICES)
-#pragma unroll
-                for (int c = 0; c < CH; ++c) {
-                    const uint64_t p0 = ba[c] + (uint64_t)(s + STAGES) * SLICE;
-                    if (p0 < bb[c]) {
-                        const uint64_t p1 = p0 + (uint64_t)PF_SLICES * SLICE;
-                        bulk_prefetch_l2(text + p0, (uint32_t)((p1 < bb[c] ? p1 : bb[c]) - p0));
-                    }
+            for (int c = 0; c < CH; ++c) {
+                if (boxes && ((boxw >> c) & 1u) && lane == 0) {
+                    const uint32_t row0 = local * CPT + c * THREADS + warp * 32;
+                    tma_load_2d(smem_addr(box_at(st, c)), &tmap, (int)(s * SLICE), (int)row0, bar0 + 8 * st);
                 }
+                if (sz[c]) bulk_copy(smem_addr(row1d(st, c)), text + ba[c] + (uint64_t)s * SLICE, sz[c], bar0 + 8 * st);
             }
         };
         for (uint32_t s = 0; s < (uint32_t)STAGES && s < nsl; ++s) issue(s);
@@ -437,8 +559,7 @@ __global__ void __launch_bounds__(THREADS)
                 for (int g = 0; g < SLICE / 16; ++g) {
                     uint4 v[CH];
 #pragma unroll
-                    for (int c = 0; c < CH; ++c)
-                        v[c] = *reinterpret_cast<const uint4 *>(rows + ((size_t)(st * CH + c) * 32 + lane) * SROW + 16 * g);
+                    for (int c = 0; c < CH; ++c) v[c] = *unit(st, c, g);
                     uint32_t q[CH], cn[CH];
 #pragma unroll
                     for (int c = 0; c < CH; ++c) {
@@ -466,10 +587,9 @@ __global__ void __launch_bounds__(THREADS)
             } else {
 #pragma unroll
                 for (int c = 0; c < CH; ++c) {
-                    const uint8_t *row = rows + ((size_t)(st * CH + c) * 32 + lane) * SROW;
                     const int32_t j0 = (int32_t)(ba[c] + (uint64_t)s * SLICE - lo[c]);
-                    for (uint32_t g = 0; g < len[c]; g += 16) {
-                        const uint4 v = *reinterpret_cast<const uint4 *>(row + g);
+                    for (uint32_t g = 0; 16 * g < len[c]; ++g) {
+                        const uint4 v = *unit(st, c, g);
                         if (constant(c)) {
                             uint32_t q = ch[c].f, cn = ch[c].cnt;
                             dfa_word(q, cn, v.x, s_dfa, A);
@@ -482,7 +602,8 @@ __global__ void __launch_bounds__(THREADS)
                             const uint32_t ws[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
                             for (int i = 0; i < 16; ++i)
-                                step(c, (ws[i >> 2] >> (8 * (i & 3))) & 0xffu, j0 + (int32_t)g + i);
+                                step(c, (ws[i >> 2] >> (8 * (i & 3))) & 0xffu, j0 + (int32_t)(16 * g) + i);
+                            if (SIMNQ) sim_compact<NQ>(V[c], ch[c]);
                         }
                     }
                 }
@@ -494,15 +615,18 @@ __global__ void __launch_bounds__(THREADS)
 #pragma unroll
         for (int c = 0; c < CH; ++c) {
             for (uint64_t p = bb[c] > lo[c] ? bb[c] : lo[c]; p < hi[c]; ++p) step(c, text[p], (int32_t)(p - lo[c]));
-            if (SIMNQ && !con[c]) {
+            if (SIMNQ) sim_compact<NQ>(V[c], ch[c]);
+            if (SIMNQ && V[c].mode != SIM_CONST) {
                 // keep the vector for the scan: id nr + global chunk index
                 const uint64_t gk = (uint64_t)gt * CPT + (uint64_t)c * THREADS + tid;
                 uint8_t *dst = S.chainvec + gk * nr;
 #pragma unroll
-                for (int i = 0; i < NQ / 4; ++i)
+                for (int i = 0; i < NQ / 4; ++i) {
+                    const uint32_t x = sim_word<NQ>(V[c], i);
 #pragma unroll
                     for (int b4 = 0; b4 < 4; ++b4)
-                        if ((uint32_t)(4 * i + b4) < nr) dst[4 * i + b4] = (V[c].w[i] >> (8 * b4)) & 0xffu;
+                        if ((uint32_t)(4 * i + b4) < nr) dst[4 * i + b4] = (x >> (8 * b4)) & 0xffu;
+                }
                 ch[c].f = nr + (uint32_t)gk;
             }
         }

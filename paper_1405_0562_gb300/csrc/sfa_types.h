@@ -40,6 +40,10 @@ struct TextDesc {
     uint32_t table;            // index into the table array (batches)
     uint32_t out_index;
     uint32_t carry;            // 1: continue from out[out_index] (Lemma 1)
+    uint32_t rows2d;           // chunks [0, rows2d) are rows of the kernel's
+                               // tensor map (full chunks of an aligned text);
+                               // 0: no tensor map
+    uint32_t pad;
 };
 
 struct TextState {             // zeroed before each launch
@@ -81,26 +85,19 @@ SFA_HD inline uint64_t num_chunks(const TextDesc &d) {
 // in bank (q + b/4) mod 32, so lanes reading the same byte value in different
 // states hit different banks (a 256-byte stride would put them all in one).
 constexpr uint32_t ROWB = 260;
-// text staging: bulk copies of SLICE bytes per chunk, STAGES in flight; rows
-// are SROW bytes apart so that 16-byte reads of 8 consecutive lanes hit
-// distinct banks
-// Every PF_SLICES slices a chunk also asks L2 to prefetch the PF_SLICES
-// slices after the ones in flight, so that the staging copies hit L2.
-#ifndef SFA_SLICE
-#define SFA_SLICE 64
-#endif
-#ifndef SFA_STAGES
-#define SFA_STAGES 2
-#endif
-#ifndef SFA_PF_SLICES
-#define SFA_PF_SLICES 4
-#endif
-constexpr int SLICE = SFA_SLICE;
-constexpr int STAGES = SFA_STAGES;
-constexpr int SROW = SLICE + 16;
-constexpr int PF_SLICES = SFA_PF_SLICES;
-static_assert(SLICE % 16 == 0, "slice of whole 16-byte words");
-static_assert((SROW / 16) % 2 == 1, "row stride an odd number of 16-byte words");
+// Text staging, SLICE bytes of every chunk per step, STAGES steps in flight.
+// For each warp, stage and round of chunks there is a BOX of 32 rows x SLICE
+// bytes: one 2-D tensor copy fills it with the next slice of the warp's 32
+// chunks (rows of the text viewed as [chunk][chunk length]), 64-byte
+// swizzled, so that 16-byte reads of 8 consecutive lanes hit distinct banks.
+// Chunks that are not a full row (the text's ragged last chunk) take a 1-D
+// bulk copy into the EXTRA row of the warp instead; without a tensor map
+// (unaligned text, forced chunk counts, batches) every lane copies its own
+// slice into its row of the box, unswizzled.
+constexpr int SLICE = 64;
+constexpr int STAGES = 2;
+constexpr int BOX = 32 * SLICE;
+static_assert(SLICE == 64, "the read pattern assumes the 64-byte swizzle");
 
 template <int THREADS, int CH>
 struct SmemLayout {
@@ -118,11 +115,16 @@ struct SmemLayout {
     static SFA_HD size_t misc_off(uint32_t nr_max) { return gpre_off(nr_max) + 32 * 4; }
     static SFA_HD size_t gvec_off(uint32_t nr_max) { return misc_off(nr_max) + 512; }
     static SFA_HD size_t bar_off(uint32_t nr_max) { return a16(gvec_off(nr_max) + (size_t)G * nr_max); }
+    // boxes: [warp][stage][round] x BOX, 1024-byte aligned (the swizzle
+    // pattern repeats every 512 bytes); extra rows: [warp][stage][round] x SLICE
     static SFA_HD size_t stage_off(uint32_t nr_max) {
-        return (bar_off(nr_max) + (size_t)NW * STAGES * 8 + 127) & ~(size_t)127;
+        return (bar_off(nr_max) + (size_t)NW * STAGES * 8 + 1023) & ~(size_t)1023;
+    }
+    static SFA_HD size_t extra_off(uint32_t nr_max) {
+        return stage_off(nr_max) + (size_t)NW * STAGES * CH * BOX;
     }
     static SFA_HD size_t bytes(uint32_t nr_max) {
-        return stage_off(nr_max) + (size_t)NW * STAGES * CH * 32 * SROW;
+        return extra_off(nr_max) + (size_t)NW * STAGES * CH * SLICE;
     }
 };
 
