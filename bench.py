@@ -34,12 +34,16 @@ import workloads as W  # noqa: E402
 
 METRIC = "text GB/s per GB300 (and % of HBM peak), bit-exact"
 PEAK_FALLBACK_GBS = 6800.0
-KERNEL_SRC = os.path.join(ROOT, "paper_1405_0562_gb300", "csrc", "sfa_device.cuh")
+KERNEL_SRCS = [os.path.join(ROOT, "paper_1405_0562_gb300", "csrc", f) for f in ("sfa_device.cuh", "sfa_types.h")]
 
 
 def kernel_hash() -> str:
-    with open(KERNEL_SRC, "rb") as fh:
-        return hashlib.sha256(fh.read()).hexdigest()[:16]
+    """Hash of the kernel's sources (the device code and its layouts)."""
+    h = hashlib.sha256()
+    for p in KERNEL_SRCS:
+        with open(p, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
 def hbm_peak():
@@ -137,13 +141,22 @@ def dist_setup(n_gpus: int):
 
 
 def barrier_max(value: float, world: int) -> float:
+    """The maximum of `value` over all ranks (device tensor under NCCL, host
+    tensor under gloo)."""
     if world <= 1:
         return value
     import torch
     import torch.distributed as dist
-    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def aggregate_gbps(bytes_per_rank: int, world: int, elapsed_s: float) -> float:
+    """Whole-job throughput of weakly scaled replicas: all ranks' bytes over
+    the slowest rank's time."""
+    return bytes_per_rank * world / barrier_max(elapsed_s, world) / 1e9
 
 
 def barrier(world: int):
@@ -177,7 +190,13 @@ def run_reference(args, rank: int, world: int):
     if rank != 0:
         return
     d, t, cfg = make_workload(args.workload, args.text_bytes)
-    sample = min(t.size, 64 << 20)
+    # per-step sample sized so that warm-up + steps take about a minute
+    cal = min(t.size, 16 << 20)
+    t0 = time.perf_counter()
+    oracle.dfa_run(d.delta, d.q0, d.accept, t[:cal])
+    speed = cal / max(time.perf_counter() - t0, 1e-6)
+    sample = int(speed * 60.0 / max(1, args.steps + args.warmup))
+    sample = max(1 << 16, min(t.size, 64 << 20, sample >> 16 << 16))
     for _ in range(max(args.warmup, 0)):
         oracle.dfa_run(d.delta, d.q0, d.accept, t[:sample])
     times = []
@@ -187,7 +206,7 @@ def run_reference(args, rank: int, world: int):
         times.append(time.perf_counter() - t0)
     total = sum(times)
     value = sample * args.steps / total / 1e9
-    desc = f"first {sample >> 20} MiB of the {t.size >> 20} MiB text per step"
+    desc = f"first {sample >> 10} KiB of the {t.size >> 20} MiB text per step"
     line = {"metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic", "config": cfg,
@@ -226,7 +245,9 @@ def run_gpu(args, rank: int, world: int, local: int):
     text = torch.from_numpy(t).to(f"cuda:{local}")
     out = sfa.empty_results(1, text.device)
     flush = None if t.size > (126 << 20) else torch.empty(256 << 20, dtype=torch.uint8, device=text.device)
-    launch = {}
+    launch = {k: v for k, v in (("chunk_bytes", args.chunk_bytes), ("block_threads", args.block_threads)) if v}
+    if launch:
+        cfg["launch"] = dict(launch)
 
     # correctness of what is timed (the oracle, when it is allowed to run)
     with torch.cuda.stream(stream):
@@ -301,20 +322,229 @@ def run_gpu(args, rank: int, world: int, local: int):
         print(json.dumps(line), flush=True)
 
 
+def _events(torch, stream, fn, steps):
+    """CUDA-event time (ms) of `steps` calls of fn on `stream`."""
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def _common(args, world, value, step_ms, cfg, peak_bytes, kern_ms, launches, clk, extra):
+    peak, peak_kind = hbm_peak()
+    achieved = peak_bytes / (kern_ms * 1e-3) / 1e9
+    line = {"metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u8", "data": "synthetic", "config": cfg,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+                         "kernel": "sfa_match_kernel", "algorithmic_bytes_per_launch": int(peak_bytes)},
+            "gpu_launches": int(launches), "clocks": clk}
+    line.update(extra)
+    return line
+
+
+def run_batched(args, rank, world, local):
+    """Config 3: 4096 texts (log-uniform 256 B .. 16 MiB, a-z) against 8
+    literal-set automata, one persistent launch per step (a CUDA graph),
+    against 4096 plain launches on one stream."""
+    import torch
+
+    import paper_1405_0562_gb300 as sfa
+    torch.cuda.set_device(local)
+    autos_d = W.workload_batch_automata()
+    autos = [sfa.Automaton.from_dfa(d) for d in autos_d]
+    lens = W.workload_batch_lengths()
+    pair = W.workload_batch_pairing(len(lens), len(autos))
+    total = int(lens.sum())
+    big = W.text_uniform(total, W.LOWER_ALPHABET, W.SEED_BATCH + 2)
+    offs = np.concatenate([[0], np.cumsum(lens)])
+    dev = torch.from_numpy(big).cuda()
+    views = [dev[offs[i]:offs[i + 1]] for i in range(len(lens))]
+    hs = [autos[p] for p in pair]
+    stream = torch.cuda.Stream()
+    b = sfa.Batch(hs, views)
+    out = sfa.empty_results(len(views))
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            b.launch(out, stream=stream, graph=True)
+    stream.synchronize()
+    got = sfa.decode(out)
+    clocks = ClockSampler(local)
+    clocks.start()
+    n0 = sfa.kernel_launch_count()
+    ms = _events(torch, stream, lambda: b.launch(out, stream=stream, graph=True), args.steps)
+    launches = sfa.kernel_launch_count() - n0
+    clk = clocks.stop()
+    step_ms = barrier_max(ms / args.steps, world)
+    # the same texts as 4096 plain launches, one stream
+    outs = sfa.empty_results(len(views))
+    plain = lambda: [hs[i].match(views[i], outs[16 * i:16 * i + 16], stream=stream) for i in range(len(views))]
+    plain()
+    rounds = max(1, min(5, args.steps))
+    pms = _events(torch, stream, plain, rounds) / rounds
+    assert sfa.decode(outs) == got
+    # spot check against the oracle
+    import oracle
+    for i in range(0, len(views), 97):
+        d = autos_d[pair[i]]
+        f, a, c = oracle.dfa_run(d.delta, d.q0, d.accept, big[offs[i]:offs[i + 1]])
+        assert got[i] == (f, a, 0, c), i
+    cfg = {"workload": "batched: 4096 texts log-uniform 256 B..16 MiB, uniform a-z, 8 literal-set automata "
+                       "(51..159 states), one persistent launch under a CUDA graph",
+           "texts": len(views), "text_bytes": total, "seed": W.SEED_BATCH, "l2": "inputs larger than L2"}
+    value = total * world / (step_ms * 1e-3) / 1e9
+    extra = {"plain_launches": {"value": total / (pms * 1e-3) / 1e9, "unit": "GB/s", "launches_per_step": len(views),
+                                "ms_per_step": pms},
+             "speedup_vs_plain": pms / step_ms}
+    line = _common(args, world, value, step_ms, cfg, total, step_ms, launches, clk, extra)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def run_sim(args, rank, world, local):
+    """Config 4: random complete DFAs with 16, 32, 64 states over 16 symbols
+    (simulation mode) on 4 GiB of uniform symbols; a step matches the text
+    with all three."""
+    import torch
+
+    import paper_1405_0562_gb300 as sfa
+    torch.cuda.set_device(local)
+    autos_d = W.workload_sim_automata()
+    autos = [sfa.Automaton.from_dfa(d) for d in autos_d]
+    assert all(a.info()["mode"] == sfa.MODE_SIM for a in autos)
+    n = args.text_bytes or (4 << 30)
+    t = W.workload_sim_text(n)
+    tt = torch.from_numpy(t).cuda()
+    stream = torch.cuda.Stream()
+    outs = [sfa.empty_results(1) for _ in autos]
+    step = lambda: [a.match(tt, o, stream=stream) for a, o in zip(autos, outs)]
+    for _ in range(args.warmup):
+        step()
+    stream.synchronize()
+    per = []
+    for a, o in zip(autos, outs):
+        per.append(_events(torch, stream, lambda: a.match(tt, o, stream=stream), 3) / 3)
+    clocks = ClockSampler(local)
+    clocks.start()
+    n0 = sfa.kernel_launch_count()
+    ms = _events(torch, stream, step, args.steps)
+    launches = sfa.kernel_launch_count() - n0
+    clk = clocks.stop()
+    step_ms = barrier_max(ms / args.steps, world)
+    got = [sfa.decode(o)[0] for o in outs]
+    import oracle
+    base = None
+    if rank == 0 and not args.no_cpu_baseline:
+        sample = min(n, 256 << 20)
+        t0 = time.perf_counter()
+        for d in autos_d:
+            oracle.dfa_run(d.delta, d.q0, d.accept, t[:sample])
+        el = time.perf_counter() - t0
+        base = {"value": 3 * sample / el / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
+                "sample": f"first {sample >> 20} MiB with each of the 3 automata"}
+    exact = None
+    if args.check:
+        exact = all(g == (f, a, 0, c) for g, (f, a, c) in
+                    zip(got, (oracle.dfa_run(d.delta, d.q0, d.accept, t) for d in autos_d)))
+    cfg = {"workload": "sim: random complete DFAs of 16/32/64 states over 16 symbols (simulation mode), "
+                       f"{n >> 20} MiB uniform over symbols 0..15, all three per step",
+           "text_bytes": n, "seed": W.SEED_SIM, "l2": "inputs larger than L2",
+           "per_automaton_GBps": {d.name: n / (p * 1e-3) / 1e9 for d, p in zip(autos_d, per)}}
+    value = 3 * n * world / (step_ms * 1e-3) / 1e9
+    extra = {"bit_exact_vs_oracle": exact}
+    if base:
+        extra["cpu_baseline"] = base
+    line = _common(args, world, value, step_ms, cfg, 3 * n, step_ms, launches, clk, extra)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def run_serving(args, rank, world, local):
+    """Config 5: Poisson arrivals of requests (log-normal lengths, median
+    64 KiB, sigma 1.5, cap 64 MiB, a-z) against 32 resident automata;
+    continuous batching vs one request at a time, at offered loads of 0.5,
+    0.8 and 0.95 of the one-at-a-time capacity."""
+    import torch
+
+    import paper_1405_0562_gb300 as sfa
+    from paper_1405_0562_gb300 import serve
+    torch.cuda.set_device(local)
+    autos_d = W.workload_serving_automata()
+    autos = [sfa.Automaton.from_dfa(d) for d in autos_d]
+    nreq = args.requests
+    _, lens, which = W.workload_serving_requests(nreq, 1.0)
+    total = int(lens.sum())
+    host = torch.from_numpy(W.text_uniform(total, W.LOWER_ALPHABET, W.SEED_SERVE + 3)).pin_memory()
+    offs = np.concatenate([[0], np.cumsum(lens)])
+    texts = [host[offs[i]:offs[i + 1]] for i in range(nreq)]
+    mean = total / nreq
+
+    def reqs(arrivals):
+        return [serve.Request(i, int(which[i]), texts[i], float(arrivals[i])) for i in range(nreq)]
+
+    # capacity of the one-at-a-time baseline (back to back, no arrivals)
+    warm = serve.one_at_a_time(autos, reqs(np.zeros(nreq))[:50], realtime=False)
+    t0 = time.perf_counter()
+    alone = serve.one_at_a_time(autos, reqs(np.zeros(nreq)), realtime=False)
+    cap = total / (time.perf_counter() - t0)
+    by_id = {r.rid: r.result for r in alone}
+    levels = {}
+    best = 0.0
+    for load in (0.5, 0.8, 0.95):
+        rate = load * cap / mean
+        arr, _, _ = W.workload_serving_requests(nreq, rate)
+        srv = serve.Server(autos, hbm_budget=4 << 30, max_batch=256, slots=3)
+        try:
+            done = srv.run(reqs(arr))
+        finally:
+            srv.close()
+        assert all(r.result == by_id[r.rid] for r in done)
+        s_stats = serve.latency_stats(done)
+        s_stats["batches"] = srv.batches
+        b_stats = serve.latency_stats(serve.one_at_a_time(autos, reqs(arr)))
+        levels[str(load)] = {"offered_GBps": load * cap / 1e9, "server": s_stats, "one_at_a_time": b_stats}
+        best = max(best, s_stats["GBps"])
+    cfg = {"workload": "serving: Poisson arrivals, log-normal lengths (median 64 KiB, sigma 1.5, cap 64 MiB), "
+                       "uniform a-z, 32 resident literal-set automata, continuous batching",
+           "requests_per_level": nreq, "text_bytes": total, "seed": W.SEED_SERVE}
+    line = {"metric": METRIC, "value": best, "unit": "GB/s", "n_gpus": world, "steps": len(levels),
+            "warmup": 1, "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u8", "data": "synthetic", "config": cfg,
+            "one_at_a_time_capacity_GBps": cap / 1e9, "levels": levels, "results_equal_alone": True}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=4000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
-    ap.add_argument("--workload", default="plain_large", choices=["plain_large", "plain_small"])
+    ap.add_argument("--workload", default="plain_large",
+                    choices=["plain_large", "plain_small", "batched", "sim", "serving"])
+    ap.add_argument("--requests", type=int, default=20000, help="serving: requests per offered load")
+    ap.add_argument("--check", action="store_true", help="sim: compare the full outputs with the oracle")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--text-bytes", type=int, default=0, help="override the text size (profiling runs only)")
+    ap.add_argument("--chunk-bytes", type=int, default=0, help="launch shape override (default: automatic)")
+    ap.add_argument("--block-threads", type=int, default=0, help="launch shape override (default: automatic)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank, world, local = dist_setup(args.gpus)
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.workload == "batched":
+        run_batched(args, rank, world, local)
+    elif args.workload == "sim":
+        run_sim(args, rank, world, local)
+    elif args.workload == "serving":
+        run_serving(args, rank, world, local)
     else:
         run_gpu(args, rank, world, local)
     if world > 1:

@@ -127,13 +127,21 @@ int choose_shape(const sfa_handle *h, uint64_t n, const sfa_launch_opts *o, Shap
     sh.threads = sim ? 128 : 256;
     sh.chains = sim ? 1 : 2;
     if (!sim) {
-        // the largest CTA (one chunk per thread) whose shared memory fits
-        const size_t optin = device_props(h->device).smem_optin;
-        for (int t : {1024, 512, 256}) {
-            if (optin == 0 || smem_bytes(t, 1, h->host.nr) <= optin) {
-                sh.threads = t;
-                sh.chains = 1;
-                break;
+        // one chunk per thread; 512-thread CTAs when two fit on an SM (one
+        // CTA's scan and look-back then overlap the other's lookups), else
+        // the largest CTA whose shared memory fits
+        sh.chains = 1;
+        const int b512 = blocks_per_sm(kernel_for(512, 1, 0, false), 512, smem_bytes(512, 1, h->host.nr));
+        if (b512 >= 2) {
+            sh.threads = 512;
+        } else {
+            const size_t optin = device_props(h->device).smem_optin;
+            sh.threads = 256;
+            for (int t : {1024, 512}) {
+                if (optin == 0 || smem_bytes(t, 1, h->host.nr) <= optin) {
+                    sh.threads = t;
+                    break;
+                }
             }
         }
     }
@@ -157,12 +165,12 @@ int choose_shape(const sfa_handle *h, uint64_t n, const sfa_launch_opts *o, Shap
         if (sh.chunk > MAX_CHUNK) return SFA_ERR_INVALID;
         return SFA_OK;
     }
-    // automatic: about six tiles per resident CTA, chunks of 256 B .. 4 KiB
+    // automatic: about three tiles per resident CTA, chunks of 256 B .. 4 KiB
     // (simulation: 4 KiB .. 64 KiB, the vector phase needs long chunks)
     const size_t smem = sfa_impl::smem_bytes(sh.threads, sh.chains, h->host.nr);
     const int bps = blocks_per_sm(sfa_impl::kernel_for(sh.threads, sh.chains, sh.simnq, false), sh.threads, smem);
     const uint64_t ctas = (uint64_t)std::max(1, bps) * std::max(1, device_props(h->device).sms);
-    uint64_t want = n / (ctas * 6 * cpt);
+    uint64_t want = n / (ctas * 3 * cpt);
     const uint64_t lo = sim ? 4096 : 256, hi = sim ? 65536 : 4096;
     want = std::min(hi, std::max(lo, align_up(want, 16)));
     sh.chunk = want;

@@ -125,8 +125,8 @@ static __device__ __noinline__ uint64_t wait_descriptor(const uint64_t *p, uint3
 // Bounded wait for the completion of an mbarrier phase (a stage of bulk
 // copies).  On giving up (timeout_us, or 2^24 polls) it raises the launch
 // error and returns; the stage's bytes are then not trusted.
-static __device__ __noinline__ void wait_stage(uint32_t bar, uint32_t parity, uint32_t *err, uint32_t timeout_us) {
-    if (mbar_try_wait(bar, parity)) return;
+static __device__ __noinline__ void wait_stage_slow(uint32_t bar, uint32_t parity, uint32_t *err,
+                                                    uint32_t timeout_us) {
     const uint64_t t0 = globaltimer();
     const uint64_t limit = (uint64_t)timeout_us * 1000ull;
     for (uint32_t it = 1;; ++it) {
@@ -136,6 +136,9 @@ static __device__ __noinline__ void wait_stage(uint32_t bar, uint32_t parity, ui
             return;
         }
     }
+}
+__device__ __forceinline__ void wait_stage(uint32_t bar, uint32_t parity, uint32_t *err, uint32_t timeout_us) {
+    if (!mbar_try_wait(bar, parity)) wait_stage_slow(bar, parity, err, timeout_us);
 }
 
 // ---------------------------------------------------------------------------
@@ -168,6 +171,15 @@ __device__ __forceinline__ void sfa_step(Chain &s, uint32_t b, int32_t j, const 
     } else {
         s.f = s_dfa[didx(s.f, b)];
         s.cnt += s.f >= first_accept;
+    }
+}
+
+// 4 symbols of a constant-state chunk, keeping the largest state seen
+__device__ __forceinline__ void dfa_word_max(uint32_t &q, uint32_t &m, uint32_t w, const uint8_t *s_dfa) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        q = s_dfa[q * ROWB + __byte_perm(w, 0, 0x4440 | j)];
+        m = max(m, q);
     }
 }
 
@@ -488,16 +500,25 @@ __global__ void __launch_bounds__(THREADS)
 
         // body: slices through shared memory
         bool reg2d[CH];          // this lane's chunk is a row of the tensor map
-        uint32_t nsl_c[CH], boxw = 0;
+        bool direct[CH];         // count every byte (see the fast path)
+        uint32_t reps[CH];       // recounted 16-byte groups
+        uint32_t nsl_c[CH], blen[CH], boxw = 0;
         uint32_t nsl = 0;
 #pragma unroll
         for (int c = 0; c < CH; ++c) {
             const uint64_t k = (uint64_t)local * CPT + (uint64_t)c * THREADS + tid;
             reg2d[c] = k < d.rows2d;
+            direct[c] = false;
+            reps[c] = 0;
             if (__ballot_sync(0xffffffffu, reg2d[c])) boxw |= 1u << c;
-            nsl_c[c] = (uint32_t)((bb[c] - ba[c] + SLICE - 1) / SLICE);
+            blen[c] = (uint32_t)(bb[c] - ba[c]);   // < 2^31: one chunk
+            nsl_c[c] = (blen[c] + SLICE - 1) / SLICE;
             nsl = nsl_c[c] > nsl ? nsl_c[c] : nsl;
         }
+        // bytes of slice s of chunk c inside the body
+        auto slice_len = [&](int c, uint32_t s) -> uint32_t {
+            return s < nsl_c[c] ? min((uint32_t)SLICE, blen[c] - s * SLICE) : 0u;
+        };
         nsl = __reduce_max_sync(0xffffffffu, nsl);
         const uint32_t nsl_box = (uint32_t)((d.chunk + SLICE - 1) / SLICE);
         // staging addresses: box of (stage, round), this lane's 1-D row, and
@@ -518,8 +539,7 @@ __global__ void __launch_bounds__(THREADS)
             uint32_t sz[CH], tot = 0;
 #pragma unroll
             for (int c = 0; c < CH; ++c) {
-                const uint64_t off = ba[c] + (uint64_t)s * SLICE;
-                sz[c] = !reg2d[c] && s < nsl_c[c] ? (uint32_t)(bb[c] - off < (uint64_t)SLICE ? bb[c] - off : SLICE) : 0u;
+                sz[c] = reg2d[c] ? 0u : slice_len(c, s);
                 tot += sz[c];
             }
             tot = __reduce_add_sync(0xffffffffu, tot);
@@ -548,42 +568,64 @@ __global__ void __launch_bounds__(THREADS)
             bool allc = true;
 #pragma unroll
             for (int c = 0; c < CH; ++c) {
-                const uint64_t off = ba[c] + (uint64_t)s * SLICE;
-                len[c] = s < nsl_c[c] ? (uint32_t)(bb[c] - off < (uint64_t)SLICE ? bb[c] - off : SLICE) : 0u;
+                len[c] = slice_len(c, s);
                 allc &= constant(c) || len[c] == 0;
             }
             if (allc) {
                 // fast path: every chunk of the thread is a constant mapping
-                // (a DFA state); one row lookup per byte, chunks interleaved
-#pragma unroll
-                for (int g = 0; g < SLICE / 16; ++g) {
+                // (a DFA state); one row lookup per byte, chunks interleaved.
+                // Per 16 bytes only the largest state is tracked; final
+                // states are the ids >= A, so a group with no final state is
+                // counted as 0 at once and the rare others are recounted
+                // exactly from the group's first state.  A chunk that needs
+                // the recount often counts every byte instead.
+                auto group = [&](int g, bool guard) {
                     uint4 v[CH];
 #pragma unroll
                     for (int c = 0; c < CH; ++c) v[c] = *unit(st, c, g);
-                    uint32_t q[CH], cn[CH];
+                    uint32_t q[CH], m[CH];
 #pragma unroll
                     for (int c = 0; c < CH; ++c) {
                         q[c] = ch[c].f;
-                        cn[c] = ch[c].cnt;
+                        m[c] = 0;
                     }
 #pragma unroll
                     for (int c = 0; c < CH; ++c)
-                        if ((uint32_t)(16 * g) < len[c]) dfa_word(q[c], cn[c], v[c].x, s_dfa, A);
+                        if (!guard || (uint32_t)(16 * g) < len[c]) {
+                            if (direct[c]) {
+                                dfa_word(q[c], ch[c].cnt, v[c].x, s_dfa, A);
+                                dfa_word(q[c], ch[c].cnt, v[c].y, s_dfa, A);
+                                dfa_word(q[c], ch[c].cnt, v[c].z, s_dfa, A);
+                                dfa_word(q[c], ch[c].cnt, v[c].w, s_dfa, A);
+                            } else {
+                                dfa_word_max(q[c], m[c], v[c].x, s_dfa);
+                                dfa_word_max(q[c], m[c], v[c].y, s_dfa);
+                                dfa_word_max(q[c], m[c], v[c].z, s_dfa);
+                                dfa_word_max(q[c], m[c], v[c].w, s_dfa);
+                                if (m[c] >= A) {
+                                    uint32_t qq = ch[c].f;
+                                    dfa_word(qq, ch[c].cnt, v[c].x, s_dfa, A);
+                                    dfa_word(qq, ch[c].cnt, v[c].y, s_dfa, A);
+                                    dfa_word(qq, ch[c].cnt, v[c].z, s_dfa, A);
+                                    dfa_word(qq, ch[c].cnt, v[c].w, s_dfa, A);
+                                    ++reps[c];
+                                }
+                            }
+                            ch[c].f = q[c];
+                        }
+                };
+                bool full = true;
 #pragma unroll
-                    for (int c = 0; c < CH; ++c)
-                        if ((uint32_t)(16 * g) < len[c]) dfa_word(q[c], cn[c], v[c].y, s_dfa, A);
+                for (int c = 0; c < CH; ++c) full &= len[c] == (uint32_t)SLICE;
+                if (full) {
 #pragma unroll
-                    for (int c = 0; c < CH; ++c)
-                        if ((uint32_t)(16 * g) < len[c]) dfa_word(q[c], cn[c], v[c].z, s_dfa, A);
+                    for (int g = 0; g < SLICE / 16; ++g) group(g, false);
+                } else {
 #pragma unroll
-                    for (int c = 0; c < CH; ++c)
-                        if ((uint32_t)(16 * g) < len[c]) dfa_word(q[c], cn[c], v[c].w, s_dfa, A);
-#pragma unroll
-                    for (int c = 0; c < CH; ++c) {
-                        ch[c].f = q[c];
-                        ch[c].cnt = cn[c];
-                    }
+                    for (int g = 0; g < SLICE / 16; ++g) group(g, true);
                 }
+#pragma unroll
+                for (int c = 0; c < CH; ++c) direct[c] = direct[c] || reps[c] * 8u > 4u * s + 32u;
             } else {
 #pragma unroll
                 for (int c = 0; c < CH; ++c) {
