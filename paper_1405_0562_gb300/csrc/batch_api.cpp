@@ -30,7 +30,8 @@ struct sfa_batch {
     int32_t cap_texts = 0;
     uint64_t cap_tiles = 0;
     uint32_t nr_max = 0;
-    size_t off_tabs = 0, off_descs = 0, off_tt = 0, mem_bytes = 0;
+    // [tables][descriptors][tensor maps][tile map]
+    size_t off_tabs = 0, off_descs = 0, off_maps = 0, off_tt = 0, mem_bytes = 0;
     uint8_t *d_mem = nullptr;
     uint8_t *d_scratch = nullptr;
     ScratchPlan plan{};
@@ -38,7 +39,7 @@ struct sfa_batch {
     // current work list
     int32_t k = 0;
     uint32_t total_tiles = 0;
-    size_t used_tabs = 0, used_descs = 0, used_tt = 0;
+    size_t used_tabs = 0, used_descs = 0, used_maps = 0, used_tt = 0;
     std::vector<int32_t> sim_index;     // texts whose handle is in simulation mode:
     std::vector<sfa_handle_t> sim_handle;   // matched one by one
     std::vector<const uint8_t *> sim_text;
@@ -58,7 +59,8 @@ namespace {
 void set_layout(sfa_batch *b) {
     b->off_tabs = 0;
     b->off_descs = align_up((size_t)b->cap_texts * sizeof(Tables), 256);
-    b->off_tt = align_up(b->off_descs + (size_t)b->cap_texts * sizeof(TextDesc), 256);
+    b->off_maps = align_up(b->off_descs + (size_t)b->cap_texts * sizeof(TextDesc), 256);
+    b->off_tt = align_up(b->off_maps + (size_t)b->cap_texts * sizeof(CUtensorMap), 256);
     b->mem_bytes = align_up(b->off_tt + (size_t)(1 + b->cap_tiles) * 4, 256);
 }
 
@@ -136,6 +138,11 @@ int fill_worklist(sfa_batch *b, const sfa_handle_t *hs, const uint8_t *const *d_
         d.table = tab_of[hs[i]];
         d.out_index = (uint32_t)i;
         d.carry = 0;
+        // the text's tensor map, in the plan's device memory
+        alignas(64) CUtensorMap map;
+        fill_text_map(d, map);
+        std::memcpy(img + b->off_maps + j * sizeof(CUtensorMap), &map, sizeof map);
+        d.map = d.rows2d ? b->d_mem + b->off_maps + j * sizeof(CUtensorMap) : nullptr;
         for (uint64_t u = 0; u < t; ++u) tt[1 + tiles + u] = (uint32_t)j;
         tiles += t;
         descs[j] = d;
@@ -145,6 +152,7 @@ int fill_worklist(sfa_batch *b, const sfa_handle_t *hs, const uint8_t *const *d_
     b->total_tiles = (uint32_t)tiles;
     b->used_tabs = distinct.size() * sizeof(Tables);
     b->used_descs = order.size() * sizeof(TextDesc);
+    b->used_maps = order.size() * sizeof(CUtensorMap);
     b->used_tt = (size_t)(1 + tiles) * 4;
     return SFA_OK;
 }
@@ -201,8 +209,8 @@ void batch_free(sfa_batch *b) {
 
 int init_shape(sfa_batch *b, const sfa_launch_opts *opts) {
     Shape &sh = b->shape;
-    sh.threads = 256;
-    sh.chains = 2;
+    sh.threads = 512;   // two CTAs per SM for automata up to ~150 states
+    sh.chains = 1;
     if (opts) {
         if (opts->block_threads) sh.threads = (int)opts->block_threads;
         if (opts->chains) sh.chains = (int)opts->chains;
@@ -343,6 +351,8 @@ int sfa_batch_update(sfa_batch_t b, const sfa_handle_t *hs, const uint8_t *const
     if (b->used_tabs) CK(cudaMemcpyAsync(b->d_mem + b->off_tabs, h + b->off_tabs, b->used_tabs, cudaMemcpyHostToDevice, s));
     if (b->used_descs)
         CK(cudaMemcpyAsync(b->d_mem + b->off_descs, h + b->off_descs, b->used_descs, cudaMemcpyHostToDevice, s));
+    if (b->used_maps)
+        CK(cudaMemcpyAsync(b->d_mem + b->off_maps, h + b->off_maps, b->used_maps, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(b->d_mem + b->off_tt, h + b->off_tt, b->used_tt, cudaMemcpyHostToDevice, s));
     CK(cudaEventRecord(b->ev_stage[st], s));
     b->stage = st;

@@ -96,6 +96,11 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map
         "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
         : "memory");
 }
+// order earlier generic writes of a tensor map in global memory before the
+// TMA unit reads it
+__device__ __forceinline__ void tensormap_acquire(const void *map) {
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(map) : "memory");
+}
 __device__ __forceinline__ void fence_proxy_async_smem() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
@@ -437,6 +442,10 @@ __global__ void __launch_bounds__(THREADS)
         const uint64_t nch = num_chunks(d);
         TextState *ts = S.texts + (BATCH ? ti : 0u);
         const uint8_t *text = d.text;
+        // the text's tensor map: the kernel parameter, or (batches) a map in
+        // device memory written before the launch, acquired for the TMA unit
+        const CUtensorMap *tmap_p = d.map ? reinterpret_cast<const CUtensorMap *>(d.map) : &tmap;
+        if (BATCH && d.map && d.rows2d && lane == 0) tensormap_acquire(d.map);
         const uint8_t *mtab = SIMNQ ? S.chainvec : T.maps;
         const uintptr_t tbase = reinterpret_cast<uintptr_t>(text);
 
@@ -554,7 +563,7 @@ __global__ void __launch_bounds__(THREADS)
             for (int c = 0; c < CH; ++c) {
                 if (boxes && ((boxw >> c) & 1u) && lane == 0) {
                     const uint32_t row0 = local * CPT + c * THREADS + warp * 32;
-                    tma_load_2d(smem_addr(box_at(st, c)), &tmap, (int)(s * SLICE), (int)row0, bar0 + 8 * st);
+                    tma_load_2d(smem_addr(box_at(st, c)), tmap_p, (int)(s * SLICE), (int)row0, bar0 + 8 * st);
                 }
                 if (sz[c]) bulk_copy(smem_addr(row1d(st, c)), text + ba[c] + (uint64_t)s * SLICE, sz[c], bar0 + 8 * st);
             }

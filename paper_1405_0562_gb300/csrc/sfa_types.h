@@ -34,6 +34,8 @@ struct TextDesc {
     const uint8_t *text;
     uint64_t n;
     uint64_t chunk;            // bytes per chunk when forced == 0
+    const void *map;           // batches: this text's tensor map in device
+                               // memory (NULL: the kernel's parameter)
     uint32_t forced;           // exact number of chunks, or 0
     uint32_t ntiles;
     uint32_t tile_base;        // first global tile of the text
