@@ -230,8 +230,9 @@ int sfa_match_host(sfa_handle_t h, const uint8_t *h_text, uint64_t n, sfa_result
  *     and live on the current device (else SFA_ERR_INVALID).
  *   - A text whose scratch would not fit is rejected with
  *     SFA_ERR_SCRATCH_LIMIT before any work is enqueued.  The scratch is about
- *     8 + nr bytes per tile of 512 chunks (nr = reachable states); with the
- *     automatic chunk sizes texts up to about 30 GB fit for nr = 256.
+ *     8 + nr bytes per tile (nr = reachable states), and the automatic chunk
+ *     length gives at most one tile per resident CTA, so every text up to the
+ *     2^40-byte maximum fits (under 100 KB for nr = 256).
  *   - All calls share the one array, and it keeps the last call's contents:
  *     each call clears the parts that must start at zero.  Calls that overlap
  *     on the GPU (two streams, two threads, two handles) race on the array and

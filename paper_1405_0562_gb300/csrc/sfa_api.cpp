@@ -165,14 +165,21 @@ int choose_shape(const sfa_handle *h, uint64_t n, const sfa_launch_opts *o, Shap
         if (sh.chunk > MAX_CHUNK) return SFA_ERR_INVALID;
         return SFA_OK;
     }
-    // automatic: about three tiles per resident CTA, chunks of 256 B .. 4 KiB
-    // (simulation: 4 KiB .. 64 KiB, the vector phase needs long chunks)
     const size_t smem = sfa_impl::smem_bytes(sh.threads, sh.chains, h->host.nr);
     const int bps = blocks_per_sm(sfa_impl::kernel_for(sh.threads, sh.chains, sh.simnq, false), sh.threads, smem);
     const uint64_t ctas = (uint64_t)std::max(1, bps) * std::max(1, device_props(h->device).sms);
-    uint64_t want = n / (ctas * 3 * cpt);
-    const uint64_t lo = sim ? 4096 : 256, hi = sim ? 65536 : 4096;
-    want = std::min(hi, std::max(lo, align_up(want, 16)));
+    uint64_t want;
+    if (sim) {
+        // about three tiles per resident CTA, chunks of 4 KiB .. 64 KiB (the
+        // vector phase needs long chunks)
+        want = std::min<uint64_t>(65536, std::max<uint64_t>(4096, align_up(n / (ctas * 3 * cpt), 16)));
+    } else {
+        // one tile per resident CTA: the scan, look-back and recount after
+        // the lookups are paid once per CTA.  Whole 64-byte slices, at least
+        // 256 bytes per chunk
+        want = std::max<uint64_t>(256, align_up((n + ctas * cpt - 1) / (ctas * cpt), (uint64_t)sfa_dev::SLICE));
+        want = std::min<uint64_t>(want, MAX_CHUNK);
+    }
     sh.chunk = want;
     return SFA_OK;
 }

@@ -230,7 +230,10 @@ def test_noalloc_refusals_need_no_device():
                                     ctypes.c_void_p]
     big = host(W.workload_large(1 << 12)[0])              # 127 states: ~135 B of scratch per tile
     fake = ctypes.c_void_p(1 << 20)                        # never dereferenced
-    assert L.sfa_match_noalloc(big.handle, fake, 1 << 40, fake, None) == sfa.ERR_SCRATCH_LIMIT
+    # automatic chunks keep the tile count at the resident CTA count, so even
+    # the longest text fits the fixed scratch; longer ones are invalid
+    assert L.sfa_match_noalloc(big.handle, fake, (1 << 40) + 1, fake, None) == sfa.ERR_INVALID
+    assert L.sfa_match_noalloc(big.handle, fake, 1 << 40, fake, None) in (sfa.ERR_NO_DEVICE, sfa.ERR_HOST_ONLY)
     assert L.sfa_match_noalloc(big.handle, None, 16, fake, None) == sfa.ERR_INVALID
     assert L.sfa_match_noalloc(big.handle, fake, 16, None, None) == sfa.ERR_INVALID
     sim = host(W.workload_sim_automata()[0])
