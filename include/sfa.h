@@ -156,6 +156,21 @@ const char *sfa_strerror(int code);
 /* ---- launch shape (all fields optional: 0 = automatic) ------------------ */
 #define SFA_DEBUG_SKIP_PUBLISH 1u  /* test knob: tile 1 never publishes its look-back
                                       descriptor, so its successor's bounded wait runs out */
+/* What a tile of the decoupled look-back is (Sect. IV's combine over chunks):
+ *   SFA_TILING_WARP  one warp's 32 consecutive chunks.  Every warp takes its
+ *                    own tiles, publishes its own descriptor and finishes its
+ *                    own tiles; single texts with chains = 1 only.
+ *   SFA_TILING_CTA   one CTA's block_threads * chains consecutive chunks,
+ *                    combined in shared memory before the look-back.  With
+ *                    automatic chunks and two CTAs per SM, a long text is cut
+ *                    into two levels of different chunk lengths: one tile per
+ *                    SM for the CTA that starts first there (the faster one)
+ *                    and a shorter one for the other.
+ *   SFA_TILING_AUTO  CTA tiles.  Batches always take CTA tiles
+ *                    (SFA_TILING_WARP: unsupported). */
+#define SFA_TILING_AUTO 0u
+#define SFA_TILING_CTA  1u
+#define SFA_TILING_WARP 2u
 
 typedef struct {
     uint32_t chunk_bytes;     /* bytes per chunk (any value >= 1; 0 = automatic) */
@@ -166,7 +181,7 @@ typedef struct {
                                  equal length (+-1 byte) instead of chunk_bytes */
     uint32_t timeout_us;      /* bound on each device-side wait (0 = 2 s) */
     uint32_t debug_flags;     /* SFA_DEBUG_* */
-    uint32_t reserved;
+    uint32_t tiling;          /* SFA_TILING_* */
 } sfa_launch_opts;
 
 /* ---- matching ------------------------------------------------------------ */

@@ -30,6 +30,7 @@ COMPILE_HOST_ONLY = 1
 STATUS_OK, STATUS_TIMEOUT = 0, 1
 DEBUG_SKIP_PUBLISH = 1
 TABLE_CLASS, TABLE_DFA, TABLE_NC, TABLE_MAPS, TABLE_ORIG = 0, 1, 2, 3, 4
+TILING_AUTO, TILING_CTA, TILING_WARP = 0, 1, 2
 RESULT_BYTES = 16
 
 # every symbol include/sfa.h declares
@@ -67,7 +68,7 @@ class LaunchOpts(ctypes.Structure):
     _fields_ = [("chunk_bytes", ctypes.c_uint32), ("block_threads", ctypes.c_uint32),
                 ("chains", ctypes.c_uint32), ("max_ctas", ctypes.c_uint32),
                 ("forced_chunks", ctypes.c_uint32), ("timeout_us", ctypes.c_uint32),
-                ("debug_flags", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+                ("debug_flags", ctypes.c_uint32), ("tiling", ctypes.c_uint32)]
 
 
 class Result(ctypes.Structure):
@@ -126,8 +127,8 @@ def _check(code: int, what: str):
 
 
 def _launch_opts(chunk_bytes=0, block_threads=0, chains=0, max_ctas=0, forced_chunks=0, timeout_us=0,
-                 debug_flags=0) -> Optional[LaunchOpts]:
-    o = LaunchOpts(chunk_bytes, block_threads, chains, max_ctas, forced_chunks, timeout_us, debug_flags, 0)
+                 debug_flags=0, tiling=0) -> Optional[LaunchOpts]:
+    o = LaunchOpts(chunk_bytes, block_threads, chains, max_ctas, forced_chunks, timeout_us, debug_flags, tiling)
     return o
 
 

@@ -16,6 +16,13 @@
 namespace sfa_impl {
 
 constexpr uint32_t DEFAULT_TIMEOUT_US = 2000000;   // 2 s per device-side wait
+constexpr uint64_t WARP_TILE_ROUNDS = 1;           // automatic chunks: warp tiles per resident warp
+// Two CTAs per SM: the share of the text (parts per million) given to the
+// level of the CTA that starts first on each SM, which runs faster
+#ifndef SFA_OLDER_SHARE_PPM
+#define SFA_OLDER_SHARE_PPM 519000
+#endif
+constexpr uint64_t OLDER_SHARE_PPM = SFA_OLDER_SHARE_PPM;
 constexpr uint64_t MAX_TEXT = 1ull << 40;
 constexpr uint64_t MAX_CHUNK = 1ull << 31;         // per-chunk counters are 32-bit
 constexpr uint32_t MAX_FORCED = 1u << 20;
@@ -57,6 +64,13 @@ struct Shape {
     int max_ctas = 0;
     uint32_t timeout_us = DEFAULT_TIMEOUT_US;
     uint32_t debug = 0;
+    bool wt = false;   // warp tiles (32 chunks per tile) instead of CTA tiles
+    bool auto_chunk = false;   // chunk length chosen by choose_shape
+    int bps = 0;               // resident CTAs per SM (automatic chunks)
+    int sms = 0;
+    uint64_t tile_chunks() const { return wt ? 32u : (uint64_t)threads * chains; }
+    // CTAs that have work for `tiles` tiles
+    uint64_t ctas_for(uint64_t tiles) const { return wt ? (tiles + threads / 32 - 1) / (threads / 32) : tiles; }
 };
 
 inline int simnq_for(uint32_t nr) { return nr <= 16 ? 16 : (nr <= 32 ? 32 : 64); }
@@ -100,9 +114,9 @@ int ensure_scratch(sfa_handle *h, size_t bytes);
 // tensor map of its full chunks and set d.rows2d; else leave d.rows2d = 0.
 void fill_text_map(sfa_dev::TextDesc &d, CUtensorMap &map);
 // enqueue one persistent kernel on `s` (tmap: the text's tensor map, or NULL)
-int launch_kernel(const void *k, int threads, size_t smem, uint32_t tiles, int max_ctas, cudaStream_t s,
+int launch_kernel(const void *k, int threads, size_t smem, uint32_t ctas, int max_ctas, cudaStream_t s,
                   const sfa_dev::Tables &tab, const sfa_dev::TextDesc &desc, const CUtensorMap *tmap,
-                  const sfa_dev::Tables *tabs,
+                  const CUtensorMap *tmap_b, const sfa_dev::Tables *tabs,
                   const sfa_dev::TextDesc *descs, const uint32_t *tile_text, const sfa_dev::Scratch &S,
                   sfa_result *out);
 // one text (sfa_match_ex / sfa_match_continue)

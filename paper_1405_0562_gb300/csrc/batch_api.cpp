@@ -168,7 +168,7 @@ int size_sim_scratch(sfa_batch *b) {
         TextDesc d{};
         d.n = b->sim_len[i];
         d.chunk = ss.chunk;
-        const uint64_t c2 = (uint64_t)ss.threads * ss.chains;
+        const uint64_t c2 = ss.tile_chunks();
         const uint64_t t = (sfa_dev::num_chunks(d) + c2 - 1) / c2;
         rc = ensure_scratch(h, plan_scratch(1, t, h->host.nr, t * c2 * h->host.nr).total);
         if (rc) return rc;
@@ -183,7 +183,7 @@ int batch_enqueue(sfa_batch *b, sfa_result *d_out, cudaStream_t s) {
         // the device, so the launch does not depend on the work list
         const uint32_t grid_tiles = b->reserved ? 0xffffffffu : b->total_tiles;
         int rc = launch_kernel(b->kernel, b->shape.threads, b->smem, grid_tiles, b->shape.max_ctas, s, Tables{},
-                               TextDesc{}, nullptr, reinterpret_cast<const Tables *>(b->d_mem + b->off_tabs),
+                               TextDesc{}, nullptr, nullptr, reinterpret_cast<const Tables *>(b->d_mem + b->off_tabs),
                                reinterpret_cast<const TextDesc *>(b->d_mem + b->off_descs),
                                reinterpret_cast<const uint32_t *>(b->d_mem + b->off_tt), b->S, d_out);
         if (rc) return rc;
@@ -218,6 +218,8 @@ int init_shape(sfa_batch *b, const sfa_launch_opts *opts) {
         sh.debug = opts->debug_flags;
         sh.max_ctas = (int)opts->max_ctas;
         if (opts->chunk_bytes > MAX_CHUNK) return SFA_ERR_INVALID;
+        if (opts->tiling > SFA_TILING_WARP) return SFA_ERR_INVALID;
+        if (opts->tiling == SFA_TILING_WARP) return SFA_ERR_UNSUPPORTED;   // batches take CTA tiles
     }
     b->kernel = kernel_for(sh.threads, sh.chains, 0, true);
     return b->kernel ? SFA_OK : SFA_ERR_UNSUPPORTED;

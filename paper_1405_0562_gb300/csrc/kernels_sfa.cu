@@ -44,7 +44,8 @@ size_t smem_bytes(int threads, int chains, uint32_t nr_max) {
     }
 }
 
-const void *kernel_for(int threads, int chains, int simnq, bool batch) {
+const void *kernel_for(int threads, int chains, int simnq, bool batch, bool wt) {
+    if (wt) return batch || chains != 1 ? nullptr : kernel_for_wt(threads, simnq);
     if (simnq == 0) return kernel_for_sfa(threads, chains, batch);
     if (batch) return nullptr;
     return kernel_for_sim(threads, chains, simnq);

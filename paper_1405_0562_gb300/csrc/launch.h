@@ -12,9 +12,11 @@ namespace sfa_impl {
 
 // The kernel instance for a launch shape, or nullptr if it is not built.
 //   simnq 0 = D-SFA mode, 16/32/64 = simulation with vectors of that size
-const void *kernel_for(int threads, int chains, int simnq, bool batch);
+//   wt = warp tiles (single texts, one chunk per thread)
+const void *kernel_for(int threads, int chains, int simnq, bool batch, bool wt = false);
 const void *kernel_for_sfa(int threads, int chains, bool batch);
 const void *kernel_for_sim(int threads, int chains, int simnq);
+const void *kernel_for_wt(int threads, int simnq);
 
 // Dynamic shared memory of a launch shape.
 size_t smem_bytes(int threads, int chains, uint32_t nr_max);

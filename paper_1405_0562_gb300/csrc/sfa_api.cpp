@@ -145,14 +145,20 @@ int choose_shape(const sfa_handle *h, uint64_t n, const sfa_launch_opts *o, Shap
             }
         }
     }
+    uint32_t tiling = SFA_TILING_AUTO;
     if (o) {
         if (o->block_threads) sh.threads = (int)o->block_threads;
         if (o->chains) sh.chains = (int)o->chains;
         if (o->timeout_us) sh.timeout_us = o->timeout_us;
         sh.debug = o->debug_flags;
         sh.max_ctas = (int)o->max_ctas;
+        tiling = o->tiling;
     }
-    if (!kernel_for(sh.threads, sh.chains, sh.simnq, false)) return SFA_ERR_UNSUPPORTED;
+    if (tiling > SFA_TILING_WARP) return SFA_ERR_INVALID;
+    // CTA tiles unless the caller asks for warp tiles (measured slower on the
+    // single-text workloads: their look-back and recount do not overlap)
+    sh.wt = tiling == SFA_TILING_WARP;
+    if (!kernel_for(sh.threads, sh.chains, sh.simnq, false, sh.wt)) return SFA_ERR_UNSUPPORTED;
     const uint64_t cpt = (uint64_t)sh.threads * sh.chains;
     if (o && o->forced_chunks) {
         if (o->forced_chunks > MAX_FORCED) return SFA_ERR_INVALID;
@@ -166,18 +172,24 @@ int choose_shape(const sfa_handle *h, uint64_t n, const sfa_launch_opts *o, Shap
         return SFA_OK;
     }
     const size_t smem = sfa_impl::smem_bytes(sh.threads, sh.chains, h->host.nr);
-    const int bps = blocks_per_sm(sfa_impl::kernel_for(sh.threads, sh.chains, sh.simnq, false), sh.threads, smem);
+    const int bps =
+        blocks_per_sm(sfa_impl::kernel_for(sh.threads, sh.chains, sh.simnq, false, sh.wt), sh.threads, smem);
     const uint64_t ctas = (uint64_t)std::max(1, bps) * std::max(1, device_props(h->device).sms);
+    sh.auto_chunk = true;
+    sh.bps = bps;
+    sh.sms = device_props(h->device).sms;
     uint64_t want;
     if (sim) {
         // about three tiles per resident CTA, chunks of 4 KiB .. 64 KiB (the
         // vector phase needs long chunks)
         want = std::min<uint64_t>(65536, std::max<uint64_t>(4096, align_up(n / (ctas * 3 * cpt), 16)));
     } else {
-        // one tile per resident CTA: the scan, look-back and recount after
-        // the lookups are paid once per CTA.  Whole 64-byte slices, at least
-        // 256 bytes per chunk
-        want = std::max<uint64_t>(256, align_up((n + ctas * cpt - 1) / (ctas * cpt), (uint64_t)sfa_dev::SLICE));
+        // CTA tiles: one tile per resident CTA, so that the scan, look-back
+        // and recount after the lookups are paid once per CTA.  Warp tiles:
+        // WARP_TILE_ROUNDS tiles per resident warp.  Whole 64-byte slices, at
+        // least 256 bytes per chunk
+        const uint64_t slots = ctas * cpt * (sh.wt ? WARP_TILE_ROUNDS : 1);
+        want = std::max<uint64_t>(256, align_up((n + slots - 1) / slots, (uint64_t)sfa_dev::SLICE));
         want = std::min<uint64_t>(want, MAX_CHUNK);
     }
     sh.chunk = want;
@@ -230,8 +242,9 @@ void fill_text_map(TextDesc &d, CUtensorMap &map) {
         d.rows2d = (uint32_t)rows;
 }
 
-int launch_kernel(const void *k, int threads, size_t smem, uint32_t tiles, int max_ctas, cudaStream_t s,
-                  const Tables &tab, const TextDesc &desc, const CUtensorMap *tmap, const Tables *tabs,
+int launch_kernel(const void *k, int threads, size_t smem, uint32_t ctas, int max_ctas, cudaStream_t s,
+                  const Tables &tab, const TextDesc &desc, const CUtensorMap *tmap, const CUtensorMap *tmap_b,
+                  const Tables *tabs,
                   const TextDesc *descs, const uint32_t *tile_text, const Scratch &S, sfa_result *out) {
     const int bps = blocks_per_sm(k, threads, smem);
     if (bps < 1) return SFA_ERR_UNSUPPORTED;
@@ -239,23 +252,62 @@ int launch_kernel(const void *k, int threads, size_t smem, uint32_t tiles, int m
     cudaGetDevice(&dev);
     uint64_t grid = (uint64_t)bps * device_props(dev).sms;
     if (max_ctas > 0) grid = std::min<uint64_t>(grid, (uint64_t)max_ctas);
-    grid = std::max<uint64_t>(1, std::min<uint64_t>(grid, tiles));
+    grid = std::max<uint64_t>(1, std::min<uint64_t>(grid, ctas));
     Tables a0 = tab;
     TextDesc a1 = desc;
-    alignas(64) CUtensorMap a2;
+    alignas(64) CUtensorMap a2, a2b;
     if (tmap)
         a2 = *tmap;
     else
         std::memset(&a2, 0, sizeof a2);
+    if (tmap_b)
+        a2b = *tmap_b;
+    else
+        std::memset(&a2b, 0, sizeof a2b);
     const Tables *a3 = tabs;
     const TextDesc *a4 = descs;
     const uint32_t *a5 = tile_text;
     Scratch a6 = S;
     sfa_result *a7 = out;
-    void *args[] = {&a0, &a1, &a2, &a3, &a4, &a5, &a6, &a7};
+    void *args[] = {&a0, &a1, &a2, &a2b, &a3, &a4, &a5, &a6, &a7};
     CK(cudaLaunchKernel(k, dim3((unsigned)grid), dim3(threads), args, smem, s));
     g_launches.fetch_add(1, std::memory_order_relaxed);
     return SFA_OK;
+}
+
+// Two levels for a text matched by two CTAs per SM with automatic chunks:
+// level A, OLDER_SHARE_PPM of the text, in one tile per SM for the CTA that
+// starts first there; level B, the rest, in one tile per SM for the other.
+// Sets the level fields of d and returns its tile count, or 0 (one level).
+uint64_t plan_two_levels(const Shape &sh, uint64_t n, TextDesc &d) {
+    if (sh.wt || sh.forced || !sh.auto_chunk || sh.bps != 2 || sh.simnq || sh.sms < 1) return 0;
+    const uint64_t cpt = sh.tile_chunks(), per = (uint64_t)sh.sms * cpt;
+    if (n < 4 * per * 256) return 0;
+    const uint64_t la = align_up((n / 1000000 * OLDER_SHARE_PPM + n % 1000000 * OLDER_SHARE_PPM / 1000000 + per - 1) / per,
+                                 (uint64_t)sfa_dev::SLICE);
+    const uint64_t split = per * la;
+    if (split >= n) return 0;
+    const uint64_t rest = n - split;
+    const uint64_t lb = std::max<uint64_t>(256, align_up((rest + per - 1) / per, (uint64_t)sfa_dev::SLICE));
+    if (la > MAX_CHUNK || lb > MAX_CHUNK) return 0;
+    d.chunk = la;
+    d.split = split;
+    d.chunk_b = lb;
+    d.split_tile = (uint32_t)sh.sms;
+    return sh.sms + ((rest + lb - 1) / lb + cpt - 1) / cpt;
+}
+
+// the tensor map of level B (d.rows2d_b), when d has two levels
+void fill_level_b_map(TextDesc &d, CUtensorMap &map_b) {
+    std::memset(&map_b, 0, sizeof map_b);
+    d.rows2d_b = 0;
+    if (!d.split_tile) return;
+    TextDesc b{};
+    b.text = d.text + d.split;
+    b.n = d.n - d.split;
+    b.chunk = d.chunk_b;
+    fill_text_map(b, map_b);
+    d.rows2d_b = b.rows2d;
 }
 
 int match_impl(sfa_handle *h, const uint8_t *d_text, uint64_t n, sfa_result *d_out, cudaStream_t s,
@@ -275,10 +327,11 @@ int match_impl(sfa_handle *h, const uint8_t *d_text, uint64_t n, sfa_result *d_o
     d.table = 0;
     d.out_index = 0;
     d.carry = carry ? 1u : 0u;
-    const uint64_t cpt = (uint64_t)sh.threads * sh.chains;
+    const uint64_t cpt = sh.tile_chunks();
     // chunk indices (and, in simulation mode, the ids nr + chunk) stay below 2^31
     if (sfa_dev::num_chunks(d) >= (1ull << 31) - 256) return SFA_ERR_INVALID;
-    const uint64_t tiles = (sfa_dev::num_chunks(d) + cpt - 1) / cpt;
+    uint64_t tiles = plan_two_levels(sh, n, d);
+    if (!tiles) tiles = (sfa_dev::num_chunks(d) + cpt - 1) / cpt;
     d.ntiles = (uint32_t)tiles;
     const uint32_t nr = h->host.nr;
     const uint64_t vec = sh.simnq ? tiles * cpt * nr : 0;
@@ -287,12 +340,13 @@ int match_impl(sfa_handle *h, const uint8_t *d_text, uint64_t n, sfa_result *d_o
     if (rc) return rc;
     CK(cudaMemsetAsync(h->d_scratch, 0, p.zero, s));
     Scratch S = make_scratch(h->d_scratch, p, nr, (uint32_t)tiles, sh);
-    const void *k = sfa_impl::kernel_for(sh.threads, sh.chains, sh.simnq, false);
+    const void *k = sfa_impl::kernel_for(sh.threads, sh.chains, sh.simnq, false, sh.wt);
     const size_t smem = sfa_impl::smem_bytes(sh.threads, sh.chains, nr);
-    alignas(64) CUtensorMap map;
+    alignas(64) CUtensorMap map, map_b;
     fill_text_map(d, map);
-    return launch_kernel(k, sh.threads, smem, (uint32_t)tiles, sh.max_ctas, s, h->dev, d, &map, nullptr, nullptr,
-                         nullptr, S, d_out);
+    fill_level_b_map(d, map_b);
+    return launch_kernel(k, sh.threads, smem, (uint32_t)sh.ctas_for(tiles), sh.max_ctas, s, h->dev, d, &map,
+                         &map_b, nullptr, nullptr, nullptr, S, d_out);
 }
 
 void free_handle_device(sfa_handle *h) {
@@ -489,20 +543,27 @@ int plan_into_scratch(sfa_handle_t h, const uint8_t *d_text, uint64_t n, const s
     if (!h || !d_out) return SFA_ERR_INVALID;
     if (n > MAX_TEXT || (n > 0 && !d_text)) return SFA_ERR_INVALID;
     if (h->host.mode != SFA_MODE_SFA) return SFA_ERR_UNSUPPORTED;
-    int rc = choose_shape(h, n, nullptr, sh);
-    if (rc) return rc;
-    d = TextDesc{};
-    d.text = d_text;
-    d.n = n;
-    d.chunk = sh.chunk;
-    d.forced = 0;
-    const uint64_t cpt = (uint64_t)sh.threads * sh.chains;
-    if (sfa_dev::num_chunks(d) >= (1ull << 31) - 256) return SFA_ERR_SCRATCH_LIMIT;
-    const uint64_t tiles = (sfa_dev::num_chunks(d) + cpt - 1) / cpt;
-    d.ntiles = (uint32_t)tiles;
-    p = plan_scratch(1, tiles, h->host.nr, 0);
-    if (p.total > cap) return SFA_ERR_SCRATCH_LIMIT;
-    return SFA_OK;
+    // the automatic shape; if its tiles need more scratch than `cap`, CTA
+    // tiles (at most one per resident CTA with automatic chunks)
+    for (uint32_t tiling : {(uint32_t)SFA_TILING_AUTO, (uint32_t)SFA_TILING_CTA}) {
+        sfa_launch_opts o{};
+        o.tiling = tiling;
+        int rc = choose_shape(h, n, &o, sh);
+        if (rc) return rc;
+        d = TextDesc{};
+        d.text = d_text;
+        d.n = n;
+        d.chunk = sh.chunk;
+        d.forced = 0;
+        const uint64_t cpt = sh.tile_chunks();
+        if (sfa_dev::num_chunks(d) >= (1ull << 31) - 256) continue;
+        uint64_t tiles = plan_two_levels(sh, n, d);
+        if (!tiles) tiles = (sfa_dev::num_chunks(d) + cpt - 1) / cpt;
+        d.ntiles = (uint32_t)tiles;
+        p = plan_scratch(1, tiles, h->host.nr, 0);
+        if (p.total <= cap) return SFA_OK;
+    }
+    return SFA_ERR_SCRATCH_LIMIT;
 }
 
 }  // namespace
@@ -530,12 +591,13 @@ int match_into_scratch(sfa_handle_t h, const uint8_t *d_text, uint64_t n, sfa_re
     // text record and the look-back descriptors
     CK(cudaMemsetAsync(scratch, 0, p.zero, s));
     const Scratch S = make_scratch(scratch, p, nr, (uint32_t)tiles, sh);
-    const void *k = kernel_for(sh.threads, sh.chains, 0, false);
+    const void *k = kernel_for(sh.threads, sh.chains, 0, false, sh.wt);
     const size_t smem = smem_bytes(sh.threads, sh.chains, nr);
-    alignas(64) CUtensorMap map;
+    alignas(64) CUtensorMap map, map_b;
     fill_text_map(d, map);
-    return launch_kernel(k, sh.threads, smem, (uint32_t)tiles, 0, s, h->dev, d, &map, nullptr, nullptr, nullptr, S,
-                         d_out);
+    fill_level_b_map(d, map_b);
+    return launch_kernel(k, sh.threads, smem, (uint32_t)sh.ctas_for(tiles), 0, s, h->dev, d, &map, &map_b, nullptr,
+                         nullptr, nullptr, S, d_out);
 }
 
 }  // namespace sfa_impl

@@ -48,6 +48,18 @@ __device__ __forceinline__ uint64_t ld_acquire(const uint64_t *p) {
 __device__ __forceinline__ void st_release(uint64_t *p, uint64_t v) {
     asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
+// a self-contained descriptor (an inclusive prefix): its readers read nothing
+// else that it would have to order
+__device__ __forceinline__ void st_relaxed(uint64_t *p, uint64_t v) {
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+// fetch-and-add that orders this thread's earlier writes before it and its
+// later reads after it
+__device__ __forceinline__ uint32_t atomic_add_acq_rel(uint32_t *p, uint32_t v) {
+    uint32_t old;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
 __device__ __forceinline__ uint64_t globaltimer() {
     uint64_t t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -375,18 +387,89 @@ __device__ __forceinline__ uint32_t dfa_count(const uint8_t *text, uint64_t p, u
 }
 
 // ---------------------------------------------------------------------------
+// tile bookkeeping shared by CTA tiles and warp tiles (run by one thread)
+// ---------------------------------------------------------------------------
+// The entering state of tile gt of a text: the start state q0 for its first
+// tile (with carry: the previous call's final state, Lemma 1), else the
+// decoupled look-back: walk back to the nearest inclusive prefix, then apply
+// the aggregates in between in order.
+__device__ __forceinline__ uint32_t tile_entering_state(const Scratch &S, const Tables &T, const TextDesc &d,
+                                                        const sfa_result *out, TextState *ts, uint32_t gt,
+                                                        uint32_t local, uint32_t nr, uint32_t nr_max) {
+    if (local == 0) {
+        if (!d.carry) return T.q0;
+        const sfa_result prev = out[d.out_index];
+        if (prev.status || prev.final_state >= T.nq_in || T.kept_of[prev.final_state] < 0) {
+            atomicOr(&ts->err, 1u);
+            return T.q0;
+        }
+        return (uint32_t)T.kept_of[prev.final_state];
+    }
+    const uint32_t base = d.tile_base;
+    uint32_t j = gt - 1;
+    uint64_t w;
+    for (;;) {
+        w = wait_descriptor(S.status + j, &S.hdr->err, S.timeout_us);
+        if ((w >> 62) == 2u || j == base) break;
+        --j;
+    }
+    uint32_t v = (uint32_t)(w & 0xffffffffu);
+    if ((w >> 62) != 2u) v = T.q0;   // unreachable: tile 0 of a text always publishes a prefix
+    if (v >= nr) v = 0;              // only after a timeout
+    for (uint32_t i = j + 1; i < gt; ++i) {
+        const uint64_t wi = ld_acquire(S.status + i);
+        if ((wi >> 62) == 2u) {
+            v = (uint32_t)(wi & 0xffffffffu);
+            if (v >= nr) v = 0;
+        } else {
+            v = S.agg[(size_t)i * nr_max + v];
+        }
+    }
+    return v;
+}
+
+// A tile is done: add its count, record the final state if it is the text's
+// last tile, and let the last tile of the text to finish write the result.
+__device__ __forceinline__ void finish_tile(const Scratch &S, const Tables &T, const TextDesc &d, TextState *ts,
+                                            sfa_result *out, unsigned long long sum, uint32_t local, uint32_t incl) {
+    if (sum) atomicAdd(&ts->count, sum);
+    if (local == d.ntiles - 1) ts->final_state = incl;
+    // release: this tile's count and final state before its `done`;
+    // acquire: every other tile's before the reads of the last one
+    const uint32_t prev = atomic_add_acq_rel(&ts->done, 1u);
+    if (prev == d.ntiles - 1) {
+        const unsigned long long total = atomicAdd(&ts->count, 0ull);
+        const uint32_t fin = *(volatile uint32_t *)&ts->final_state;
+        const uint32_t err = *(volatile uint32_t *)&ts->err | *(volatile uint32_t *)&S.hdr->err;
+        sfa_result r;
+        r.final_state = (uint32_t)T.orig_of[fin < T.nr ? fin : 0];
+        r.accept_final = fin >= T.first_accept ? 1 : 0;
+        r.status = err ? SFA_STATUS_TIMEOUT : SFA_STATUS_OK;
+        r.reserved = 0;
+        r.count = (d.carry ? out[d.out_index].count : 0ull) + total;
+        out[d.out_index] = r;
+    }
+}
+
+// ---------------------------------------------------------------------------
 // the persistent kernel
 //   SIMNQ = 0: D-SFA mode; SIMNQ = 16/32/64: simulation mode with vectors of
 //   that many entries (the kept states, padded)
 //   BATCH: tables and texts come from device arrays, else from `tab`/`desc`
+//   WT: warp tiles.  Every warp takes its own tiles of 32 chunks, publishes
+//   its own look-back descriptor and finishes its own tiles, with no CTA
+//   barrier after the tables are staged: a warp's scan and look-back overlap
+//   the other warps' lookups, and slower warps take fewer tiles.  One text,
+//   one chunk per thread.  Without WT a tile is the CTA's THREADS * CH chunks.
 // ---------------------------------------------------------------------------
-template <int THREADS, int CH, int SIMNQ, bool BATCH>
+template <int THREADS, int CH, int SIMNQ, bool BATCH, bool WT = false>
 __global__ void __launch_bounds__(THREADS)
-    sfa_match_kernel(Tables tab, TextDesc desc, const __grid_constant__ CUtensorMap tmap, const Tables *tabs,
-                     const TextDesc *descs,
+    sfa_match_kernel(Tables tab, TextDesc desc, const __grid_constant__ CUtensorMap tmap,
+                     const __grid_constant__ CUtensorMap tmap_b, const Tables *tabs, const TextDesc *descs,
                      const uint32_t *tile_text, Scratch S, sfa_result *out) {
     using L = SmemLayout<THREADS, CH>;
     constexpr int CPT = L::CPT, NW = L::NW, G = L::G;
+    static_assert(!WT || (!BATCH && CH == 1), "warp tiles: one text, one chunk per thread");
     constexpr int NQ = SIMNQ > 0 ? SIMNQ : 4;
     extern __shared__ __align__(128) uint8_t smem[];
     const uint32_t nr_max = S.nr_max;
@@ -410,44 +493,97 @@ __global__ void __launch_bounds__(THREADS)
     __syncwarp();
     uint32_t parity = 0;             // bit s: phase parity expected next on stage s (warp-uniform)
     uint32_t loaded = 0xffffffffu;   // table index in shared memory (CTA-uniform)
+    // stage the DFA rows (ROWB apart) and the class table; all threads
+    auto stage_tables = [&](const Tables &T, uint32_t idx) {
+        const uint32_t *src = reinterpret_cast<const uint32_t *>(T.dfa);
+        for (uint32_t i = tid; i < T.nr * 64; i += THREADS)
+            *reinterpret_cast<uint32_t *>(s_dfa + (i >> 6) * ROWB + (i & 63) * 4) = __ldg(src + i);
+        if (tid < 16) reinterpret_cast<uint4 *>(s_cls)[tid] = __ldg(reinterpret_cast<const uint4 *>(T.cls) + tid);
+        loaded = idx;
+        __syncthreads();
+    };
+
+    // Two levels: the first CTA to start on an SM takes level-A tiles, later
+    // ones level-B tiles (the older CTA of an SM runs faster, so its tiles
+    // are longer); each moves to the other level once its own runs out.
+    const bool two_levels = !BATCH && !WT && desc.split_tile != 0;
+    uint32_t slot = 0;   // thread 0: CTAs that started on this SM before this one
+    if (two_levels && tid == 0) {
+        uint32_t smid;
+        asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+        slot = atomicAdd(&S.hdr->sm_slot[smid & 255u], 1u);
+    }
+    auto grab = [&]() -> uint32_t {
+        if (!two_levels) return atomicAdd(&S.hdr->tile_ctr, 1u);
+        const uint32_t na = desc.split_tile, all = S.total_tiles;
+        uint32_t t;
+        if (slot == 0) {
+            t = atomicAdd(&S.hdr->tile_ctr, 1u);
+            if (t >= na) t = na + atomicAdd(&S.hdr->tile_ctr_b, 1u);
+        } else {
+            t = na + atomicAdd(&S.hdr->tile_ctr_b, 1u);
+            if (t >= all) {
+                t = atomicAdd(&S.hdr->tile_ctr, 1u);
+                if (t >= na) t = all;
+            }
+        }
+        return t;
+    };
 
     for (;;) {
-        if (tid == 0) {
-            s_misc->tile = atomicAdd(&S.hdr->tile_ctr, 1u);
-            s_misc->gconst = 0;
+        uint32_t gt = 0;
+        if constexpr (WT) {
+            if (lane == 0) gt = atomicAdd(&S.hdr->tile_ctr, 1u);
+            gt = __shfl_sync(0xffffffffu, gt, 0);
+        } else {
+            if (tid == 0) {
+                s_misc->tile = grab();
+                s_misc->gconst = 0;
+            }
+            __syncthreads();
+            gt = s_misc->tile;
         }
-        __syncthreads();
-        const uint32_t gt = s_misc->tile;
         // a batch reads its tile count from the work list (tile_text[0]), so a
         // plan can be refilled without changing its launch
         const uint32_t total = BATCH ? __ldg(tile_text) : S.total_tiles;
-        if (gt >= total) break;
+        if (gt >= total) {
+            // warp tiles: a warp without a first tile still takes its part in
+            // staging the tables (the one CTA barrier of the launch)
+            if (WT && loaded != 0u) stage_tables(tab, 0u);
+            break;
+        }
 
         uint32_t ti = 0;
         if (BATCH) ti = __ldg(tile_text + 1 + gt);
         const TextDesc d = BATCH ? descs[ti] : desc;
         const Tables T = BATCH ? tabs[d.table] : tab;
         const uint32_t tabidx = BATCH ? d.table : 0u;
-        if (tabidx != loaded) {
-            // stage the DFA rows (ROWB apart) and the class table
-            const uint32_t *src = reinterpret_cast<const uint32_t *>(T.dfa);
-            for (uint32_t i = tid; i < T.nr * 64; i += THREADS)
-                *reinterpret_cast<uint32_t *>(s_dfa + (i >> 6) * ROWB + (i & 63) * 4) = __ldg(src + i);
-            if (tid < 16) reinterpret_cast<uint4 *>(s_cls)[tid] = __ldg(reinterpret_cast<const uint4 *>(T.cls) + tid);
-            loaded = tabidx;
-            __syncthreads();
-        }
         const uint32_t nr = T.nr, A = T.first_accept;
         const uint32_t local = gt - d.tile_base;
-        const uint64_t nch = num_chunks(d);
+        // the tile's level: its byte range [lbase, lend), chunk length, tile
+        // index within the level and full chunks of the level's tensor map
+        const bool lvb = d.split_tile != 0 && local >= d.split_tile;
+        const uint32_t lt = lvb ? local - d.split_tile : local;
+        const uint64_t lbase = lvb ? d.split : 0;
+        const uint64_t lend = d.split_tile != 0 && !lvb ? d.split : d.n;
+        const uint64_t lchunk = lvb ? d.chunk_b : d.chunk;
+        const uint32_t lrows = lvb ? d.rows2d_b : d.rows2d;
+        uint64_t nch = d.forced ? d.forced : (lend - lbase + lchunk - 1) / lchunk;
+        if (nch == 0) nch = 1;   // the empty text: one empty chunk
         TextState *ts = S.texts + (BATCH ? ti : 0u);
         const uint8_t *text = d.text;
         // the text's tensor map: the kernel parameter, or (batches) a map in
         // device memory written before the launch, acquired for the TMA unit
-        const CUtensorMap *tmap_p = d.map ? reinterpret_cast<const CUtensorMap *>(d.map) : &tmap;
+        const CUtensorMap *tmap_p = lvb ? &tmap_b : (d.map ? reinterpret_cast<const CUtensorMap *>(d.map) : &tmap);
         if (BATCH && d.map && d.rows2d && lane == 0) tensormap_acquire(d.map);
         const uint8_t *mtab = SIMNQ ? S.chainvec : T.maps;
         const uintptr_t tbase = reinterpret_cast<uintptr_t>(text);
+        // index within the level of this thread's chunk c, and of the first
+        // chunk of the warp's 32 in that round
+        auto kidx = [&](int c) -> uint64_t {
+            return WT ? (uint64_t)lt * 32 + lane : (uint64_t)lt * CPT + (uint64_t)c * THREADS + tid;
+        };
+        auto krow0 = [&](int c) -> uint32_t { return WT ? lt * 32u : lt * CPT + c * THREADS + warp * 32; };
 
         // ---------------- pass 1: every chunk from f_I ----------------
         Chain ch[CH];
@@ -455,15 +591,15 @@ __global__ void __launch_bounds__(THREADS)
         uint64_t lo[CH], hi[CH], ba[CH], bb[CH];
 #pragma unroll
         for (int c = 0; c < CH; ++c) {
-            const uint64_t k = (uint64_t)local * CPT + (uint64_t)c * THREADS + tid;
+            const uint64_t k = kidx(c);
             if (k >= nch) {
-                lo[c] = hi[c] = d.n;
+                lo[c] = hi[c] = lend;
             } else if (d.forced) {
                 lo[c] = k * d.n / d.forced;
                 hi[c] = (k + 1) * d.n / d.forced;
             } else {
-                lo[c] = k * d.chunk;
-                hi[c] = lo[c] + d.chunk < d.n ? lo[c] + d.chunk : d.n;
+                lo[c] = lbase + k * lchunk;
+                hi[c] = lo[c] + lchunk < lend ? lo[c] + lchunk : lend;
             }
             // body: the 16-byte-aligned addresses inside [lo, hi)
             const uint64_t a = (((tbase + lo[c]) + 15) & ~(uintptr_t)15) - tbase;
@@ -502,11 +638,6 @@ __global__ void __launch_bounds__(THREADS)
         };
         auto constant = [&](int c) -> bool { return SIMNQ ? V[c].mode == SIM_CONST : ch[c].f < nr; };
 
-        // head bytes
-#pragma unroll
-        for (int c = 0; c < CH; ++c)
-            for (uint64_t p = lo[c]; p < ba[c]; ++p) step(c, text[p], (int32_t)(p - lo[c]));
-
         // body: slices through shared memory
         bool reg2d[CH];          // this lane's chunk is a row of the tensor map
         bool direct[CH];         // count every byte (see the fast path)
@@ -515,8 +646,8 @@ __global__ void __launch_bounds__(THREADS)
         uint32_t nsl = 0;
 #pragma unroll
         for (int c = 0; c < CH; ++c) {
-            const uint64_t k = (uint64_t)local * CPT + (uint64_t)c * THREADS + tid;
-            reg2d[c] = k < d.rows2d;
+            const uint64_t k = kidx(c);
+            reg2d[c] = k < lrows;
             direct[c] = false;
             reps[c] = 0;
             if (__ballot_sync(0xffffffffu, reg2d[c])) boxw |= 1u << c;
@@ -529,14 +660,14 @@ __global__ void __launch_bounds__(THREADS)
             return s < nsl_c[c] ? min((uint32_t)SLICE, blen[c] - s * SLICE) : 0u;
         };
         nsl = __reduce_max_sync(0xffffffffu, nsl);
-        const uint32_t nsl_box = (uint32_t)((d.chunk + SLICE - 1) / SLICE);
+        const uint32_t nsl_box = (uint32_t)((lchunk + SLICE - 1) / SLICE);
         // staging addresses: box of (stage, round), this lane's 1-D row, and
         // the 16-byte unit g of this lane's slice
         auto box_at = [&](uint32_t st, int c) -> uint8_t * {
             return s_box + ((size_t)(st * CH + c)) * BOX;
         };
         auto row1d = [&](uint32_t st, int c) -> uint8_t * {
-            return d.rows2d ? s_extra + (size_t)(st * CH + c) * SLICE : box_at(st, c) + lane * SLICE;
+            return lrows ? s_extra + (size_t)(st * CH + c) * SLICE : box_at(st, c) + lane * SLICE;
         };
         auto unit = [&](uint32_t st, int c, uint32_t g) -> const uint4 * {
             const uint8_t *p = reg2d[c] ? box_at(st, c) + lane * SLICE + ((g ^ ((uint32_t)(lane >> 1) & 3u)) << 4)
@@ -562,13 +693,23 @@ __global__ void __launch_bounds__(THREADS)
 #pragma unroll
             for (int c = 0; c < CH; ++c) {
                 if (boxes && ((boxw >> c) & 1u) && lane == 0) {
-                    const uint32_t row0 = local * CPT + c * THREADS + warp * 32;
+                    const uint32_t row0 = krow0(c);
                     tma_load_2d(smem_addr(box_at(st, c)), tmap_p, (int)(s * SLICE), (int)row0, bar0 + 8 * st);
                 }
                 if (sz[c]) bulk_copy(smem_addr(row1d(st, c)), text + ba[c] + (uint64_t)s * SLICE, sz[c], bar0 + 8 * st);
             }
         };
+        // the first slices are in flight while the tables are staged
         for (uint32_t s = 0; s < (uint32_t)STAGES && s < nsl; ++s) issue(s);
+        // (warp tiles: every warp comes here once, in its first tile, or in
+        // the exit branch above)
+        if (tabidx != loaded) stage_tables(T, tabidx);
+
+        // head bytes
+#pragma unroll
+        for (int c = 0; c < CH; ++c)
+            for (uint64_t p = lo[c]; p < ba[c]; ++p) step(c, text[p], (int32_t)(p - lo[c]));
+
         for (uint32_t s = 0; s < nsl; ++s) {
             const uint32_t st = s % STAGES;
             wait_stage(bar0 + 8 * st, (parity >> st) & 1u, &S.hdr->err, S.timeout_us);
@@ -669,7 +810,7 @@ __global__ void __launch_bounds__(THREADS)
             if (SIMNQ) sim_compact<NQ>(V[c], ch[c]);
             if (SIMNQ && V[c].mode != SIM_CONST) {
                 // keep the vector for the scan: id nr + global chunk index
-                const uint64_t gk = (uint64_t)gt * CPT + (uint64_t)c * THREADS + tid;
+                const uint64_t gk = WT ? (uint64_t)gt * 32 + lane : (uint64_t)gt * CPT + (uint64_t)c * THREADS + tid;
                 uint8_t *dst = S.chainvec + gk * nr;
 #pragma unroll
                 for (int i = 0; i < NQ / 4; ++i) {
@@ -682,10 +823,68 @@ __global__ void __launch_bounds__(THREADS)
             }
         }
 
-        // ---------------- scan of the chunk mappings inside the tile ----------------
 #pragma unroll
         for (int c = 0; c < CH; ++c) s_f[c * THREADS + tid] = ch[c].f;
         __syncwarp();   // chunk vectors of the simulation path written by this warp
+        if constexpr (WT) {
+            // ---------------- warp tile: summary, look-back, pass 2 ----------------
+            const uint32_t fl = ch[0].f;
+            const uint32_t cm = __ballot_sync(0xffffffffu, fl < nr);
+            uint64_t *st = S.status + gt;
+            uint8_t *gv = s_gvec + (size_t)warp * nr;   // this warp's |Q|-vector
+            const bool skip = (S.debug & SFA_DEBUG_SKIP_PUBLISH) && local == 1;
+            uint32_t tval = 0;
+            if (cm) {
+                // constant: the last constant chunk composed with the chunks
+                // after it; an inclusive prefix at once
+                const int lc = 31 - __clz(cm);
+                tval = __shfl_sync(0xffffffffu, fl, lc);
+                for (int i = lc + 1; i < 32; ++i) tval = apply_map(__shfl_sync(0xffffffffu, fl, i), tval, mtab, nr);
+                if (lane == 0 && !skip) st_relaxed(st, ST_PREFIX | tval);
+            } else {
+                // a |Q|-vector: lanes take the components, every chunk in
+                // turn; published as the tile's aggregate
+                uint8_t *agg = S.agg + (size_t)gt * nr_max;
+                for (uint32_t qb = 0; qb < nr; qb += 32) {
+                    const uint32_t q = qb + lane;
+                    uint32_t v = q < nr ? q : 0u;
+                    for (int i = 0; i < 32; ++i) v = apply_map(__shfl_sync(0xffffffffu, fl, i), v, mtab, nr);
+                    if (q < nr) {
+                        gv[q] = (uint8_t)v;
+                        agg[q] = (uint8_t)v;
+                    }
+                }
+                __threadfence();
+                __syncwarp();
+                if (lane == 0 && local > 0 && !skip) st_release(st, ST_AGG);
+            }
+            uint32_t s_in = 0, incl = tval;
+            if (lane == 0) {
+                s_in = tile_entering_state(S, T, d, out, ts, gt, local, nr, nr_max);
+                if (!cm) {
+                    incl = gv[s_in];
+                    if (!skip) st_relaxed(st, ST_PREFIX | incl);
+                }
+            }
+            s_in = __shfl_sync(0xffffffffu, s_in, 0);
+            // entering state of every chunk: the nearest constant chunk below
+            // it (or s_in), then the chunks in between; pass 2
+            const uint32_t below = cm & lanemask_lt;
+            const int j = below ? 31 - __clz(below) : -1;
+            uint32_t v = __shfl_sync(0xffffffffu, fl, j < 0 ? 0 : j);
+            if (j < 0) v = s_in;
+            for (int i = j + 1; i < lane; ++i) v = apply_map(s_f[warp * 32 + i], v, mtab, nr);
+            unsigned long long tsum = ch[0].cnt;
+            if (ch[0].lm >= 0)
+                tsum = dfa_count(text, lo[0], lo[0] + (uint64_t)ch[0].lm + 1, v, s_dfa, A) + ch[0].cnt - ch[0].snap;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) tsum += __shfl_down_sync(0xffffffffu, tsum, o);
+            if (lane == 0) finish_tile(S, T, d, ts, out, tsum, local, incl);
+            __syncwarp();
+            continue;
+        }
+
+        // ---------------- scan of the chunk mappings inside the tile ----------------
         uint32_t my_gconst = 0;   // bit c: the group of round c is constant (warp-uniform)
 #pragma unroll
         for (int c = 0; c < CH; ++c) {
@@ -731,7 +930,7 @@ __global__ void __launch_bounds__(THREADS)
                 const int gc = 31 - __clz(gconst);
                 tval = s_gval[gc];
                 for (int g = gc + 1; g < G; ++g) tval = s_gvec[(size_t)g * nr + tval];
-                if (lane == 0 && !skip) st_release(st, ST_PREFIX | tval);
+                if (lane == 0 && !skip) st_relaxed(st, ST_PREFIX | tval);
             } else {
                 for (uint32_t qb = 0; qb < nr; qb += 32) {
                     const uint32_t q = qb + lane;
@@ -748,48 +947,12 @@ __global__ void __launch_bounds__(THREADS)
             // entering state of the tile
             uint32_t s_in = 0;
             if (lane == 0) {
-                if (local == 0) {
-                    if (d.carry) {
-                        const sfa_result prev = out[d.out_index];
-                        if (prev.status || prev.final_state >= T.nq_in || T.kept_of[prev.final_state] < 0) {
-                            atomicOr(&ts->err, 1u);
-                            s_in = T.q0;
-                        } else {
-                            s_in = (uint32_t)T.kept_of[prev.final_state];
-                        }
-                    } else {
-                        s_in = T.q0;
-                    }
-                } else {
-                    // decoupled look-back: walk back to the nearest inclusive
-                    // prefix, then apply the aggregates in between in order
-                    const uint32_t base = d.tile_base;
-                    uint32_t j = gt - 1;
-                    uint64_t w;
-                    for (;;) {
-                        w = wait_descriptor(S.status + j, &S.hdr->err, S.timeout_us);
-                        if ((w >> 62) == 2u || j == base) break;
-                        --j;
-                    }
-                    uint32_t v = (uint32_t)(w & 0xffffffffu);
-                    if ((w >> 62) != 2u) v = T.q0;   // unreachable: tile 0 of a text always publishes a prefix
-                    if (v >= nr) v = 0;              // only after a timeout
-                    for (uint32_t i = j + 1; i < gt; ++i) {
-                        const uint64_t wi = ld_acquire(S.status + i);
-                        if ((wi >> 62) == 2u) {
-                            v = (uint32_t)(wi & 0xffffffffu);
-                            if (v >= nr) v = 0;
-                        } else {
-                            v = S.agg[(size_t)i * nr_max + v];
-                        }
-                    }
-                    s_in = v;
-                }
+                s_in = tile_entering_state(S, T, d, out, ts, gt, local, nr, nr_max);
                 uint32_t incl = tval;
                 if (!tconst) {
                     incl = s_in;
                     for (int g = 0; g < G; ++g) incl = s_gvec[(size_t)g * nr + incl];
-                    if (!skip) st_release(st, ST_PREFIX | incl);
+                    if (!skip) st_relaxed(st, ST_PREFIX | incl);
                 }
                 s_misc->s_in = s_in;
                 s_misc->incl = incl;
@@ -839,24 +1002,7 @@ __global__ void __launch_bounds__(THREADS)
         if (tid == 0) {
             unsigned long long sum = 0;
             for (int w = 0; w < NW; ++w) sum += s_misc->wsum[w];
-            if (sum) atomicAdd(&ts->count, sum);
-            if (local == d.ntiles - 1) ts->final_state = s_misc->incl;
-            __threadfence();
-            const uint32_t prev = atomicAdd(&ts->done, 1u);
-            if (prev == d.ntiles - 1) {
-                // the last tile of this text to finish writes its result
-                __threadfence();
-                const unsigned long long total = atomicAdd(&ts->count, 0ull);
-                const uint32_t fin = *(volatile uint32_t *)&ts->final_state;
-                const uint32_t err = *(volatile uint32_t *)&ts->err | *(volatile uint32_t *)&S.hdr->err;
-                sfa_result r;
-                r.final_state = (uint32_t)T.orig_of[fin < nr ? fin : 0];
-                r.accept_final = fin >= A ? 1 : 0;
-                r.status = err ? SFA_STATUS_TIMEOUT : SFA_STATUS_OK;
-                r.reserved = 0;
-                r.count = (d.carry ? out[d.out_index].count : 0ull) + total;
-                out[d.out_index] = r;
-            }
+            finish_tile(S, T, d, ts, out, sum, local, s_misc->incl);
         }
         __syncthreads();
     }

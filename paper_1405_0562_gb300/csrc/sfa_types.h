@@ -33,9 +33,17 @@ struct Tables {
 struct TextDesc {
     const uint8_t *text;
     uint64_t n;
-    uint64_t chunk;            // bytes per chunk when forced == 0
+    uint64_t chunk;            // bytes per chunk when forced == 0 (level A)
     const void *map;           // batches: this text's tensor map in device
                                // memory (NULL: the kernel's parameter)
+    // Two levels (split_tile != 0): tiles [0, split_tile) cover [0, split)
+    // in chunks of `chunk` bytes, the others [split, n) in chunks of
+    // chunk_b bytes, rows of the kernel's second tensor map (rows2d_b full
+    // ones).  split_tile == 0: one level, [0, n) in chunks of `chunk`.
+    uint64_t split;
+    uint64_t chunk_b;
+    uint32_t split_tile;
+    uint32_t rows2d_b;
     uint32_t forced;           // exact number of chunks, or 0
     uint32_t ntiles;
     uint32_t tile_base;        // first global tile of the text
@@ -57,9 +65,11 @@ struct TextState {             // zeroed before each launch
 };
 
 struct LaunchHeader {          // zeroed before each launch
-    uint32_t tile_ctr;
+    uint32_t tile_ctr;         // next tile (two levels: next level-A tile)
     uint32_t err;
-    uint32_t pad[14];
+    uint32_t tile_ctr_b;       // two levels: next level-B tile
+    uint32_t pad[13];
+    uint32_t sm_slot[256];     // two levels: CTAs started so far on each SM
 };
 
 struct Scratch {

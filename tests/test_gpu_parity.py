@@ -109,6 +109,66 @@ def test_launch_shapes(threads, chains, chunk):
         assert gpu_match(a, t, block_threads=threads, chains=chains, chunk_bytes=chunk) == expect(d, t), name
 
 
+@pytest.mark.parametrize("name", ["ab_star", "r5", "ac_set", "T4", "rand8", "kmp", "one_state"])
+@pytest.mark.parametrize("n", [0, 1, 33, 4096, 100_003, 1 << 21])
+def test_tilings_agree(name, n):
+    """Warp tiles and CTA tiles: the same results as the oracle."""
+    sfa = sfa_mod()
+    d = AUTOMATA[name]()
+    a = sfa.Automaton.from_dfa(d)
+    t = text_for(d, n, seed=n + 3)
+    want = expect(d, t)
+    for tiling in (sfa.TILING_WARP, sfa.TILING_CTA):
+        for threads in (256, 512, 1024):
+            for chunk in (0, 16, 64, 1000):
+                got = gpu_match(a, t, block_threads=threads, chains=1, chunk_bytes=chunk, tiling=tiling)
+                assert got == want, (tiling, threads, chunk)
+
+
+@pytest.mark.parametrize("name", ["rand8", "T4", "even_odd5", "r3"])
+def test_tilings_agree_simulation(name):
+    sfa = sfa_mod()
+    d = AUTOMATA[name]()
+    a = sfa.Automaton(d.delta, d.q0, d.accept, mode=sfa.MODE_SIM)
+    for n in (0, 77, 70_001, 1 << 20):
+        t = text_for(d, n, seed=n + 5)
+        want = expect(d, t)
+        for tiling in (sfa.TILING_WARP, sfa.TILING_CTA):
+            for threads in (128, 256):
+                for chunk in (0, 16, 4096):
+                    got = gpu_match(a, t, block_threads=threads, chains=1, chunk_bytes=chunk, tiling=tiling)
+                    assert got == want, (tiling, threads, chunk, n)
+
+
+@pytest.mark.parametrize("n", [80 << 20, (96 << 20) + 4093])
+def test_two_level_text(n):
+    """Long texts with automatic chunks take two levels of chunk lengths;
+    also unaligned (level B then has no tensor map) and under max_ctas."""
+    sfa = sfa_mod()
+    d, t = W.workload_large(n)
+    a = sfa.Automaton.from_dfa(d)
+    want = expect(d, t)
+    assert gpu_match(a, t) == want
+    buf = torch.from_numpy(np.concatenate([np.zeros(3, np.uint8), t])).cuda()
+    out = a.match(buf[3:])
+    torch.cuda.synchronize()
+    assert sfa.decode(out)[0] == want
+    assert gpu_match(a, t, max_ctas=100) == want
+
+
+def test_warp_tiles_with_max_ctas():
+    """Warp-tile look-back over thousands of tiles with few resident CTAs."""
+    sfa = sfa_mod()
+    for name in ("r5", "ac_set", "T4"):
+        d = AUTOMATA[name]()
+        a = sfa.Automaton.from_dfa(d)
+        t = text_for(d, 300_000, seed=1)
+        for ctas in (1, 2, 7):
+            got = gpu_match(a, t, chunk_bytes=16, block_threads=256, chains=1, max_ctas=ctas,
+                            tiling=sfa.TILING_WARP)
+            assert got == expect(d, t)
+
+
 def test_many_tiles_with_max_ctas():
     """Look-back over hundreds of tiles with few resident CTAs."""
     for name in ("r5", "ac_set", "T4"):
@@ -253,6 +313,13 @@ def test_timeout_status_is_reported():
     assert time.time() - t0 < 30
     assert got[2] == sfa.STATUS_TIMEOUT
     assert gpu_match(a, t, chunk_bytes=16, block_threads=128, chains=1) == expect(d, t)
+    # the same with warp tiles: warp tile 1 never publishes
+    t0 = time.time()
+    got = gpu_match(a, t, chunk_bytes=16, block_threads=256, chains=1, timeout_us=50_000,
+                    debug_flags=sfa.DEBUG_SKIP_PUBLISH, tiling=sfa.TILING_WARP)
+    assert time.time() - t0 < 30
+    assert got[2] == sfa.STATUS_TIMEOUT
+    assert gpu_match(a, t, chunk_bytes=16, block_threads=256, chains=1, tiling=sfa.TILING_WARP) == expect(d, t)
 
 
 # ---------------------------------------------------------------------------
