@@ -180,9 +180,11 @@ int choose_shape(const sfa_handle *h, uint64_t n, const sfa_launch_opts *o, Shap
     sh.sms = device_props(h->device).sms;
     uint64_t want;
     if (sim) {
-        // about three tiles per resident CTA, chunks of 4 KiB .. 64 KiB (the
-        // vector phase needs long chunks)
-        want = std::min<uint64_t>(65536, std::max<uint64_t>(4096, align_up(n / (ctas * 3 * cpt), 16)));
+        // one tile per resident CTA, chunks of at least 4 KiB: every chunk
+        // starts with the vector phase (up to |Q| lookups per byte until its
+        // entries converge), so chunks are made as long as the CTAs allow
+        want = std::max<uint64_t>(4096, align_up((n + ctas * cpt - 1) / (ctas * cpt), (uint64_t)sfa_dev::SLICE));
+        want = std::min<uint64_t>(want, MAX_CHUNK);
     } else {
         // CTA tiles: one tile per resident CTA, so that the scan, look-back
         // and recount after the lookups are paid once per CTA.  Warp tiles:

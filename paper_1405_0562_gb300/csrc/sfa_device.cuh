@@ -462,8 +462,18 @@ __device__ __forceinline__ void finish_tile(const Scratch &S, const Tables &T, c
 //   the other warps' lookups, and slower warps take fewer tiles.  One text,
 //   one chunk per thread.  Without WT a tile is the CTA's THREADS * CH chunks.
 // ---------------------------------------------------------------------------
+// CTAs per SM asked of the register allocator (0: none asked): the batch
+// instances with one chunk per thread must run 1024 threads per SM (two CTAs
+// of 512, ...), which their allocator does not choose by itself; the others
+// are left to it (a bound there measured 4 % slower on the single-text kernel
+// at the same register count)
+template <int THREADS, int CH, int SIMNQ, bool BATCH>
+constexpr int min_ctas_per_sm() {
+    return BATCH && SIMNQ == 0 && CH == 1 && THREADS <= 1024 ? 1024 / THREADS : 0;
+}
+
 template <int THREADS, int CH, int SIMNQ, bool BATCH, bool WT = false>
-__global__ void __launch_bounds__(THREADS)
+__global__ void __launch_bounds__(THREADS, (min_ctas_per_sm<THREADS, CH, SIMNQ, BATCH>()))
     sfa_match_kernel(Tables tab, TextDesc desc, const __grid_constant__ CUtensorMap tmap,
                      const __grid_constant__ CUtensorMap tmap_b, const Tables *tabs, const TextDesc *descs,
                      const uint32_t *tile_text, Scratch S, sfa_result *out) {
@@ -764,10 +774,49 @@ __global__ void __launch_bounds__(THREADS)
                             ch[c].f = q[c];
                         }
                 };
-                bool full = true;
+                // full slices and no chunk counting every byte: the CH chains
+                // advance byte by byte in one block, so that their lookups
+                // overlap
+                auto group_fast = [&](int g) {
+                    uint4 v[CH];
+                    uint32_t q[CH], m[CH];
 #pragma unroll
-                for (int c = 0; c < CH; ++c) full &= len[c] == (uint32_t)SLICE;
-                if (full) {
+                    for (int c = 0; c < CH; ++c) {
+                        v[c] = *unit(st, c, g);
+                        q[c] = ch[c].f;
+                        m[c] = 0;
+                    }
+#pragma unroll
+                    for (int i = 0; i < 16; ++i)
+#pragma unroll
+                        for (int c = 0; c < CH; ++c) {
+                            const uint32_t w = (i >> 2) == 0 ? v[c].x : (i >> 2) == 1 ? v[c].y : (i >> 2) == 2 ? v[c].z : v[c].w;
+                            q[c] = s_dfa[q[c] * ROWB + __byte_perm(w, 0, 0x4440 | (i & 3))];
+                            m[c] = max(m[c], q[c]);
+                        }
+#pragma unroll
+                    for (int c = 0; c < CH; ++c) {
+                        if (m[c] >= A) {
+                            uint32_t qq = ch[c].f;
+                            dfa_word(qq, ch[c].cnt, v[c].x, s_dfa, A);
+                            dfa_word(qq, ch[c].cnt, v[c].y, s_dfa, A);
+                            dfa_word(qq, ch[c].cnt, v[c].z, s_dfa, A);
+                            dfa_word(qq, ch[c].cnt, v[c].w, s_dfa, A);
+                            ++reps[c];
+                        }
+                        ch[c].f = q[c];
+                    }
+                };
+                bool full = true, anydirect = false;
+#pragma unroll
+                for (int c = 0; c < CH; ++c) {
+                    full &= len[c] == (uint32_t)SLICE;
+                    anydirect |= direct[c];
+                }
+                if (full && !anydirect) {
+#pragma unroll
+                    for (int g = 0; g < SLICE / 16; ++g) group_fast(g);
+                } else if (full) {
 #pragma unroll
                     for (int g = 0; g < SLICE / 16; ++g) group(g, false);
                 } else {
