@@ -301,6 +301,19 @@ int sfa_batch_reserve(int32_t max_texts, uint64_t max_tiles, uint32_t nr_max, co
 int sfa_batch_update(sfa_batch_t b, const sfa_handle_t *hs, const uint8_t *const *d_texts, const uint64_t *lens,
                      int32_t k, sfa_stream_t stream);
 
+/*
+ * sfa_batch_update_host -- sfa_batch_update for texts still on the host: for
+ * each i, enqueues one asynchronous copy of lens[i] bytes from h_texts[i]
+ * (host; pinned, else the copy is synchronous) to d_dst[i] (device, the
+ * caller's buffer) on `stream`, then replaces the work list by the k texts
+ * at d_dst (as sfa_batch_update).  The serving loop's copy-in, with no
+ * per-request runtime call from Python; the paper has no counterpart.
+ * Errors as sfa_batch_update, plus CUDA when a copy cannot be enqueued
+ * (copies enqueued before the failure stay enqueued).
+ */
+int sfa_batch_update_host(sfa_batch_t b, const sfa_handle_t *hs, const uint8_t *const *h_texts,
+                          uint8_t *const *d_dst, const uint64_t *lens, int32_t k, sfa_stream_t stream);
+
 /* sfa_batch_launch -- enqueue the planned work; d_out: device, k results in
  * the order of the texts given to sfa_batch_create.  Launches of one plan
  * must not overlap on the GPU. */

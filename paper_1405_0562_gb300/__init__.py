@@ -39,7 +39,7 @@ EXPORTED = (
     "sfa_match", "sfa_match_ex", "sfa_match_continue", "sfa_match_host",
     "sfa_batch_create", "sfa_batch_launch", "sfa_batch_graph_launch", "sfa_batch_destroy",
     "sfa_match_batch", "sfa_kernel_launch_count", "sfa_match_noalloc",
-    "sfa_batch_reserve", "sfa_batch_update",
+    "sfa_batch_reserve", "sfa_batch_update", "sfa_batch_update_host",
 )
 
 
@@ -110,6 +110,7 @@ def lib():
     L.sfa_match_noalloc.argtypes = [P, P, u64, P, P]
     L.sfa_batch_reserve.argtypes = [i32, u64, u32, ctypes.POINTER(LaunchOpts), ctypes.POINTER(P)]
     L.sfa_batch_update.argtypes = [P, P, P, P, i32, P]
+    L.sfa_batch_update_host.argtypes = [P, P, P, P, P, i32, P]
     for name in EXPORTED:
         if name not in ("sfa_destroy", "sfa_batch_destroy", "sfa_strerror", "sfa_kernel_launch_count"):
             getattr(L, name).restype = ctypes.c_int

@@ -361,6 +361,20 @@ int sfa_batch_update(sfa_batch_t b, const sfa_handle_t *hs, const uint8_t *const
     return SFA_OK;
 }
 
+int sfa_batch_update_host(sfa_batch_t b, const sfa_handle_t *hs, const uint8_t *const *h_texts,
+                          uint8_t *const *d_dst, const uint64_t *lens, int32_t k, sfa_stream_t stream) {
+    if (!b || !b->reserved || k < 0 || k > b->cap_texts) return SFA_ERR_INVALID;
+    if (k > 0 && (!h_texts || !d_dst || !lens)) return SFA_ERR_INVALID;
+    for (int32_t i = 0; i < k; ++i)
+        if (lens[i] && (!h_texts[i] || !d_dst[i])) return SFA_ERR_INVALID;
+    int rc = check_inputs(hs, reinterpret_cast<const uint8_t *const *>(d_dst), lens, k, b->device);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    for (int32_t i = 0; i < k; ++i)
+        if (lens[i]) CK(cudaMemcpyAsync(d_dst[i], h_texts[i], lens[i], cudaMemcpyHostToDevice, s));
+    return sfa_batch_update(b, hs, reinterpret_cast<const uint8_t *const *>(d_dst), lens, k, stream);
+}
+
 int sfa_batch_launch(sfa_batch_t b, sfa_result *d_out, sfa_stream_t stream) {
     if (!b || (b->k > 0 && !d_out)) return SFA_ERR_INVALID;
     return batch_enqueue(b, d_out, (cudaStream_t)stream);

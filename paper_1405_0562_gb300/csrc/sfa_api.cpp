@@ -188,10 +188,11 @@ int choose_shape(const sfa_handle *h, uint64_t n, const sfa_launch_opts *o, Shap
     } else {
         // CTA tiles: one tile per resident CTA, so that the scan, look-back
         // and recount after the lookups are paid once per CTA.  Warp tiles:
-        // WARP_TILE_ROUNDS tiles per resident warp.  Whole 64-byte slices, at
-        // least 256 bytes per chunk
+        // WARP_TILE_ROUNDS tiles per resident warp.  Whole 64-byte slices (a
+        // short text takes one slice per chunk: its latency is then the
+        // kernel's fixed cost plus one slice)
         const uint64_t slots = ctas * cpt * (sh.wt ? WARP_TILE_ROUNDS : 1);
-        want = std::max<uint64_t>(256, align_up((n + slots - 1) / slots, (uint64_t)sfa_dev::SLICE));
+        want = std::max<uint64_t>(sfa_dev::SLICE, align_up((n + slots - 1) / slots, (uint64_t)sfa_dev::SLICE));
         want = std::min<uint64_t>(want, MAX_CHUNK);
     }
     sh.chunk = want;

@@ -430,25 +430,29 @@ __device__ __forceinline__ uint32_t tile_entering_state(const Scratch &S, const 
 
 // A tile is done: add its count, record the final state if it is the text's
 // last tile, and let the last tile of the text to finish write the result.
+// A text of one tile writes it at once.
 __device__ __forceinline__ void finish_tile(const Scratch &S, const Tables &T, const TextDesc &d, TextState *ts,
                                             sfa_result *out, unsigned long long sum, uint32_t local, uint32_t incl) {
-    if (sum) atomicAdd(&ts->count, sum);
-    if (local == d.ntiles - 1) ts->final_state = incl;
-    // release: this tile's count and final state before its `done`;
-    // acquire: every other tile's before the reads of the last one
-    const uint32_t prev = atomic_add_acq_rel(&ts->done, 1u);
-    if (prev == d.ntiles - 1) {
-        const unsigned long long total = atomicAdd(&ts->count, 0ull);
-        const uint32_t fin = *(volatile uint32_t *)&ts->final_state;
-        const uint32_t err = *(volatile uint32_t *)&ts->err | *(volatile uint32_t *)&S.hdr->err;
-        sfa_result r;
-        r.final_state = (uint32_t)T.orig_of[fin < T.nr ? fin : 0];
-        r.accept_final = fin >= T.first_accept ? 1 : 0;
-        r.status = err ? SFA_STATUS_TIMEOUT : SFA_STATUS_OK;
-        r.reserved = 0;
-        r.count = (d.carry ? out[d.out_index].count : 0ull) + total;
-        out[d.out_index] = r;
+    unsigned long long total = sum;
+    uint32_t fin = incl;
+    if (d.ntiles > 1) {
+        if (sum) atomicAdd(&ts->count, sum);
+        if (local == d.ntiles - 1) ts->final_state = incl;
+        // release: this tile's count and final state before its `done`;
+        // acquire: every other tile's before the reads of the last one
+        const uint32_t prev = atomic_add_acq_rel(&ts->done, 1u);
+        if (prev != d.ntiles - 1) return;
+        total = atomicAdd(&ts->count, 0ull);
+        fin = *(volatile uint32_t *)&ts->final_state;
     }
+    const uint32_t err = *(volatile uint32_t *)&ts->err | *(volatile uint32_t *)&S.hdr->err;
+    sfa_result r;
+    r.final_state = (uint32_t)T.orig_of[fin < T.nr ? fin : 0];
+    r.accept_final = fin >= T.first_accept ? 1 : 0;
+    r.status = err ? SFA_STATUS_TIMEOUT : SFA_STATUS_OK;
+    r.reserved = 0;
+    r.count = (d.carry ? out[d.out_index].count : 0ull) + total;
+    out[d.out_index] = r;
 }
 
 // ---------------------------------------------------------------------------
@@ -930,6 +934,8 @@ __global__ void __launch_bounds__(THREADS, (min_ctas_per_sm<THREADS, CH, SIMNQ, 
             for (int o = 16; o > 0; o >>= 1) tsum += __shfl_down_sync(0xffffffffu, tsum, o);
             if (lane == 0) finish_tile(S, T, d, ts, out, tsum, local, incl);
             __syncwarp();
+            // every warp of the grid had at most one tile: no second grab
+            if (!BATCH && S.total_tiles <= gridDim.x * (uint32_t)NW) break;
             continue;
         }
 
@@ -1054,6 +1060,9 @@ __global__ void __launch_bounds__(THREADS, (min_ctas_per_sm<THREADS, CH, SIMNQ, 
             finish_tile(S, T, d, ts, out, sum, local, s_misc->incl);
         }
         __syncthreads();
+        // every CTA of the grid had at most one tile (each CTA takes one
+        // per grab): no second grab
+        if (!BATCH && S.total_tiles <= gridDim.x) break;
     }
 }
 

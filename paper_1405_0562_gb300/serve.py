@@ -82,6 +82,19 @@ class Request:
         return int(self.text.numel() if hasattr(self.text, "numel") else len(self.text))
 
 
+def _host_ptr(text) -> int:
+    """Address of a request's host bytes (a CPU tensor, preferably pinned, or
+    a contiguous numpy array)."""
+    if hasattr(text, "data_ptr"):
+        if text.is_cuda or not text.is_contiguous():
+            raise ValueError("request text must be a contiguous host tensor")
+        return text.data_ptr() if text.numel() else 0
+    a = np.asarray(text)
+    if a.dtype != np.uint8 or not a.flags["C_CONTIGUOUS"]:
+        raise ValueError("request text must be contiguous uint8")   # no temporary copy may be read
+    return a.ctypes.data if a.size else 0
+
+
 class _Slot:
     def __init__(self, torch, max_texts, max_tiles, nr_max, opts, device):
         self.stream = torch.cuda.Stream(device=device)
@@ -104,7 +117,7 @@ class Server:
     """Continuous batching over resident automata with HBM-budget admission."""
 
     def __init__(self, automata: Sequence[Automaton], hbm_budget: int = 4 << 30, max_batch: int = 512,
-                 slots: int = 3, chunk_bytes: int = 1024, device=None):
+                 slots: int = 3, chunk_bytes: int = 1024, block_threads: int = 512, device=None):
         import torch
         self.torch = torch
         self.device = device or torch.device("cuda", torch.cuda.current_device())
@@ -113,8 +126,8 @@ class Server:
         self.arena = torch.empty(hbm_budget, dtype=torch.uint8, device=self.device)
         self.alloc = ArenaAllocator(hbm_budget)
         self.max_batch = max_batch
-        self.opts = LaunchOpts(chunk_bytes, 256, 2, 0, 0, 0, 0, 0)
-        cpt = 256 * 2
+        self.opts = LaunchOpts(chunk_bytes, block_threads, 1, 0, 0, 0, 0, 0)
+        cpt = block_threads
         max_tiles = max_batch + hbm_budget // (cpt * chunk_bytes) + 1
         self.slots = [_Slot(torch, max_batch, max_tiles, nr_max, self.opts, self.device) for _ in range(slots)]
         self.free_slots = deque(self.slots)
@@ -171,14 +184,14 @@ class Server:
             base = self.arena.data_ptr()
             ptrs = (ctypes.c_void_p * k)(*[base + r.offset for r in take])
             lens = (ctypes.c_uint64 * k)(*[r.nbytes for r in take])
+            srcs = (ctypes.c_void_p * k)(*[_host_ptr(r.text) for r in take])
+            for r in take:
+                r.admitted = now
             with torch.cuda.stream(slot.stream):
-                for r in take:
-                    r.admitted = now
-                    if r.nbytes:
-                        src = r.text if hasattr(r.text, "numel") else torch.from_numpy(np.asarray(r.text))
-                        self.arena[r.offset:r.offset + r.nbytes].copy_(src, non_blocking=True)
                 sp = _stream_ptr(slot.stream)
-                _check(lib().sfa_batch_update(slot.plan, hs, ptrs, lens, k, sp), "sfa_batch_update")
+                # copies of the texts into the arena and the new work list,
+                # enqueued natively on the slot's stream
+                _check(lib().sfa_batch_update_host(slot.plan, hs, srcs, ptrs, lens, k, sp), "sfa_batch_update_host")
                 _check(lib().sfa_batch_launch(slot.plan, slot.out.data_ptr(), sp), "sfa_batch_launch")
                 slot.out_host[:k * RESULT_BYTES].copy_(slot.out[:k * RESULT_BYTES], non_blocking=True)
                 slot.event.record(slot.stream)

@@ -61,6 +61,49 @@ def test_reserved_plan_refilled(sfa):
         L.sfa_batch_destroy(plan)
 
 
+def test_reserved_plan_refilled_from_host(sfa):
+    """sfa_batch_update_host: pinned host texts copied into a device arena
+    and matched by the refilled plan, several rounds on one stream."""
+    autos_d = W.workload_serving_automata(5)
+    autos = [sfa.Automaton.from_dfa(d) for d in autos_d]
+    nr_max = max(a.info()["n_reachable"] for a in autos)
+    L = sfa.lib()
+    opts = sfa.LaunchOpts(1024, 512, 1, 0, 0, 0, 0, 0)
+    plan = ctypes.c_void_p()
+    assert L.sfa_batch_reserve(64, 8192, nr_max, ctypes.byref(opts), ctypes.byref(plan)) == sfa.OK
+    stream = torch.cuda.Stream()
+    arena = torch.empty(64 << 20, dtype=torch.uint8, device="cuda")
+    rng = np.random.default_rng(2)
+    try:
+        for rnd in range(4):
+            k = int(rng.integers(1, 50))
+            lens = [int(x) for x in rng.integers(0, 500_000, k)]
+            which = [int(x) for x in rng.integers(0, len(autos), k)]
+            texts = [torch.from_numpy(W.text_uniform(n, W.LOWER_ALPHABET, 70 * rnd + i)).pin_memory()
+                     for i, n in enumerate(lens)]
+            offs = np.concatenate([[0], np.cumsum([(n + 255) // 256 * 256 for n in lens])])
+            assert offs[-1] <= arena.numel()
+            hs = (ctypes.c_void_p * k)(*[autos[j].handle.value for j in which])
+            src = (ctypes.c_void_p * k)(*[t.data_ptr() if t.numel() else 0 for t in texts])
+            dst = (ctypes.c_void_p * k)(*[arena.data_ptr() + int(o) for o in offs[:k]])
+            ln = (ctypes.c_uint64 * k)(*lens)
+            out = torch.zeros(16 * 64, dtype=torch.uint8, device="cuda")
+            torch.cuda.synchronize()
+            assert L.sfa_batch_update_host(plan, hs, src, dst, ln, k, stream.cuda_stream) == sfa.OK
+            assert L.sfa_batch_launch(plan, out.data_ptr(), stream.cuda_stream) == sfa.OK
+            stream.synchronize()
+            got = sfa.decode(out[:16 * k])
+            assert got == [expect(autos_d[j], t.numpy()) for j, t in zip(which, texts)], rnd
+        # NULL host pointer with a nonzero length: refused before any copy
+        bad = (ctypes.c_void_p * 1)(0)
+        one = (ctypes.c_uint64 * 1)(10)
+        h1 = (ctypes.c_void_p * 1)(autos[0].handle.value)
+        d1 = (ctypes.c_void_p * 1)(arena.data_ptr())
+        assert L.sfa_batch_update_host(plan, h1, bad, d1, one, 1, stream.cuda_stream) == sfa.ERR_INVALID
+    finally:
+        L.sfa_batch_destroy(plan)
+
+
 def test_reserved_plan_refuses_over_capacity(sfa):
     """A real text that needs more tiles than the plan holds is refused by
     sfa_batch_update (nothing is launched)."""
