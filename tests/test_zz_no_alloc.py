@@ -41,7 +41,8 @@ def noalloc(sfa, a, text, out, stream):
 
 
 def test_noalloc_equals_match_twice(sfa):
-    cases = [W.workload_large(48 << 20), W.workload_single()]
+    # 96 MiB: long enough for the two-level split of automatic chunks
+    cases = [W.workload_large(48 << 20), W.workload_large(96 << 20), W.workload_single()]
     d3 = W.dfa_rn(4)
     t3 = np.frombuffer(b"01235678" * 100_000 + b"0", dtype=np.uint8).copy()
     t3[::9973] = ord("9")
