@@ -18,7 +18,7 @@ import os
 import threading
 from typing import Dict, List, Optional
 
-from . import MODE_SIM, SfaError, empty_results
+from . import MODE_SIM, TILING_WARP, SfaError, empty_results
 
 _LOCK = threading.Lock()
 
@@ -63,15 +63,19 @@ def key_for(info: dict, n: int, device_name: str) -> str:
 
 
 def candidates(info: dict, n: int) -> List[Dict[str, int]]:
+    """The automatic shape first (one tile per resident CTA, two levels on
+    long texts), then CTA shapes with fixed chunk lengths, then warp tiles."""
     sim = info["mode"] == MODE_SIM
     shapes = SIM_SHAPES if sim else SFA_SHAPES
     chunks = SIM_CHUNKS if sim else SFA_CHUNKS
-    out = []
+    out = [{}]
     for th, ch in shapes:
         for c in chunks:
             if c * th * ch > max(n, 1) * 2 and c > chunks[0]:
                 continue   # a single tile would hold the text many times over
             out.append({"block_threads": th, "chains": ch, "chunk_bytes": c})
+    for th in ((128, 256) if sim else (256, 512, 1024)):
+        out.append({"block_threads": th, "chains": 1, "tiling": TILING_WARP})
     return out
 
 
