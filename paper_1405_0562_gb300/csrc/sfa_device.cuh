@@ -428,16 +428,25 @@ __device__ __forceinline__ uint32_t tile_entering_state(const Scratch &S, const 
     return v;
 }
 
+// Part of a tile's count (and the final state if it is the text's last
+// tile), for a text of several tiles.
+__device__ __forceinline__ void add_tile_count(const TextDesc &d, TextState *ts, unsigned long long sum,
+                                               uint32_t local, uint32_t incl) {
+    if (sum) atomicAdd(&ts->count, sum);
+    if (local == d.ntiles - 1) ts->final_state = incl;
+}
+
 // A tile is done: add its count, record the final state if it is the text's
 // last tile, and let the last tile of the text to finish write the result.
-// A text of one tile writes it at once.
+// A text of one tile writes it at once.  counted: the count and final state
+// were added already (add_tile_count).
 __device__ __forceinline__ void finish_tile(const Scratch &S, const Tables &T, const TextDesc &d, TextState *ts,
-                                            sfa_result *out, unsigned long long sum, uint32_t local, uint32_t incl) {
+                                            sfa_result *out, unsigned long long sum, uint32_t local, uint32_t incl,
+                                            bool counted = false) {
     unsigned long long total = sum;
     uint32_t fin = incl;
     if (d.ntiles > 1) {
-        if (sum) atomicAdd(&ts->count, sum);
-        if (local == d.ntiles - 1) ts->final_state = incl;
+        if (!counted) add_tile_count(d, ts, sum, local, incl);
         // release: this tile's count and final state before its `done`;
         // acquire: every other tile's before the reads of the last one
         const uint32_t prev = atomic_add_acq_rel(&ts->done, 1u);
@@ -453,6 +462,33 @@ __device__ __forceinline__ void finish_tile(const Scratch &S, const Tables &T, c
     r.reserved = 0;
     r.count = (d.carry ? out[d.out_index].count : 0ull) + total;
     out[d.out_index] = r;
+}
+
+// A tile whose count still lacks the recount of its first chunk over
+// [lo, lo + lm] from the tile's entering state (a constant tile whose first
+// chunk is constant: nothing else depends on the entering state).  Resolved
+// by the CTA after its next tile has streamed, when the look-back no longer
+// waits; the recount reads the DFA rows in global memory (the shared copy may
+// hold another automaton by then).
+// (kept by thread 0 in the CTA's Misc record)
+template <bool BATCH>
+__device__ __noinline__ void resolve_deferred(Misc *m, const Scratch &S, const Tables &tab, const TextDesc &desc,
+                                              const Tables *tabs, const TextDesc *descs, sfa_result *out) {
+    const uint32_t gt = m->dfr_gt, ti = m->dfr_ti;
+    const TextDesc d = BATCH ? descs[ti] : desc;
+    const Tables T = BATCH ? tabs[d.table] : tab;
+    TextState *ts = S.texts + (BATCH ? ti : 0u);
+    const uint32_t local = gt - d.tile_base;
+    uint32_t q = tile_entering_state(S, T, d, out, ts, gt, local, T.nr, S.nr_max);
+    unsigned long long c = 0;
+    const uint64_t lo = m->dfr_lo, e = lo + (uint64_t)m->dfr_lm;
+    for (uint64_t p = lo; p <= e; ++p) {
+        q = __ldg(T.dfa + (size_t)q * 256 + d.text[p]);
+        c += q >= T.first_accept;
+    }
+    if (c) atomicAdd(&ts->count, c);
+    finish_tile(S, T, d, ts, out, 0ull, local, 0u, true);
+    m->dfr_valid = 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -527,6 +563,10 @@ __global__ void __launch_bounds__(THREADS, (min_ctas_per_sm<THREADS, CH, SIMNQ, 
         asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
         slot = atomicAdd(&S.hdr->sm_slot[smid & 255u], 1u);
     }
+    // deferred first-chunk recounts: batches (a CTA takes many tiles there;
+    // single texts take one tile per CTA with automatic chunks)
+    constexpr bool DEFER = BATCH && !WT;
+    if (tid == 0) s_misc->dfr_valid = 0;
     auto grab = [&]() -> uint32_t {
         if (!two_levels) return atomicAdd(&S.hdr->tile_ctr, 1u);
         const uint32_t na = desc.split_tile, all = S.total_tiles;
@@ -564,6 +604,7 @@ __global__ void __launch_bounds__(THREADS, (min_ctas_per_sm<THREADS, CH, SIMNQ, 
             // warp tiles: a warp without a first tile still takes its part in
             // staging the tables (the one CTA barrier of the launch)
             if (WT && loaded != 0u) stage_tables(tab, 0u);
+            if (DEFER && tid == 0 && s_misc->dfr_valid) resolve_deferred<BATCH>(s_misc, S, tab, desc, tabs, descs, out);
             break;
         }
 
@@ -713,8 +754,10 @@ __global__ void __launch_bounds__(THREADS, (min_ctas_per_sm<THREADS, CH, SIMNQ, 
                 if (sz[c]) bulk_copy(smem_addr(row1d(st, c)), text + ba[c] + (uint64_t)s * SLICE, sz[c], bar0 + 8 * st);
             }
         };
-        // the first slices are in flight while the tables are staged
+        // the first slices are in flight while the previous tile's deferred
+        // recount is resolved and the tables are staged
         for (uint32_t s = 0; s < (uint32_t)STAGES && s < nsl; ++s) issue(s);
+        if (DEFER && tid == 0 && s_misc->dfr_valid) resolve_deferred<BATCH>(s_misc, S, tab, desc, tabs, descs, out);
         // (warp tiles: every warp comes here once, in its first tile, or in
         // the exit branch above)
         if (tabidx != loaded) stage_tables(T, tabidx);
@@ -999,10 +1042,24 @@ __global__ void __launch_bounds__(THREADS, (min_ctas_per_sm<THREADS, CH, SIMNQ, 
                 __syncwarp();
                 if (lane == 0 && local > 0 && !skip) st_release(st, ST_AGG);
             }
-            // entering state of the tile
+            // entering state of the tile.  A constant tile whose first chunk
+            // is constant needs it only for that chunk's recount: none if the
+            // chunk has no mixed position, else (if the CTA will take another
+            // tile) deferred until after that tile
             uint32_t s_in = 0;
             if (lane == 0) {
-                s_in = tile_entering_state(S, T, d, out, ts, gt, local, nr, nr_max);
+                const bool first_const = DEFER && tconst && local > 0 && ch[0].f < nr && total > gridDim.x;
+                if (first_const && ch[0].lm < 0) {
+                    s_in = 0;   // unused
+                } else if (first_const && ch[0].lm < 64) {
+                    s_misc->dfr_gt = gt;
+                    s_misc->dfr_ti = ti;
+                    s_misc->dfr_lo = lo[0];
+                    s_misc->dfr_lm = ch[0].lm;
+                    s_misc->dfr_valid = 1;
+                } else {
+                    s_in = tile_entering_state(S, T, d, out, ts, gt, local, nr, nr_max);
+                }
                 uint32_t incl = tval;
                 if (!tconst) {
                     incl = s_in;
@@ -1044,11 +1101,15 @@ __global__ void __launch_bounds__(THREADS, (min_ctas_per_sm<THREADS, CH, SIMNQ, 
             uint32_t v = __shfl_sync(0xffffffffu, fl, j < 0 ? 0 : j);
             if (j < 0) v = s_gpre[g];
             for (int i = j + 1; i < lane; ++i) v = apply_map(s_f[g * 32 + i], v, mtab, nr);
-            uint32_t total = ch[c].cnt;
+            uint32_t cc = ch[c].cnt;
             if (ch[c].lm >= 0) {
-                total = dfa_count(text, lo[c], lo[c] + (uint64_t)ch[c].lm + 1, v, s_dfa, A) + ch[c].cnt - ch[c].snap;
+                // the tile's first chunk with a deferred recount: only the
+                // positions after its last mixed one now
+                const bool deferred = DEFER && c == 0 && tid == 0 && s_misc->dfr_valid;
+                cc = (deferred ? 0u : dfa_count(text, lo[c], lo[c] + (uint64_t)ch[c].lm + 1, v, s_dfa, A)) +
+                     ch[c].cnt - ch[c].snap;
             }
-            tsum += total;
+            tsum += cc;
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) tsum += __shfl_down_sync(0xffffffffu, tsum, o);
@@ -1057,7 +1118,10 @@ __global__ void __launch_bounds__(THREADS, (min_ctas_per_sm<THREADS, CH, SIMNQ, 
         if (tid == 0) {
             unsigned long long sum = 0;
             for (int w = 0; w < NW; ++w) sum += s_misc->wsum[w];
-            finish_tile(S, T, d, ts, out, sum, local, s_misc->incl);
+            if (DEFER && s_misc->dfr_valid)
+                add_tile_count(d, ts, sum, local, s_misc->incl);   // done when the recount is resolved
+            else
+                finish_tile(S, T, d, ts, out, sum, local, s_misc->incl);
         }
         __syncthreads();
         // every CTA of the grid had at most one tile (each CTA takes one

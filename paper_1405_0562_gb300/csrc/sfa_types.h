@@ -151,7 +151,11 @@ struct Misc {
     uint32_t gconst;        // bit g: group g is a constant mapping
     uint32_t s_in;          // entering state of the tile
     uint32_t incl;          // state after the tile
-    uint32_t pad[4];
+    // thread 0: a tile whose first chunk's recount is deferred (valid != 0)
+    uint32_t dfr_gt, dfr_ti, dfr_valid;
+    int32_t dfr_lm;
+    unsigned long long dfr_lo;
+    unsigned long long pad;
     unsigned long long wsum[32];
 };
 static_assert(sizeof(Misc) <= 512, "misc region");
