@@ -468,8 +468,8 @@ def run_serving(args, rank, world, local):
     """Config 5: Poisson arrivals of requests (log-normal lengths, median
     64 KiB, sigma 1.5, cap 64 MiB, a-z) against 32 resident automata;
     continuous batching vs one request at a time, at offered loads of 0.5,
-    0.8 and 0.95 of the one-at-a-time capacity, and past it (2, 5, 10 and
-    20 times), where requests queue up for the one-at-a-time loop."""
+    0.8 and 0.95 of the one-at-a-time capacity, and past it (2, 5, 10, 20
+    and 50 times), where requests queue up for the one-at-a-time loop."""
     import torch
 
     import paper_1405_0562_gb300 as sfa
@@ -496,7 +496,7 @@ def run_serving(args, rank, world, local):
     by_id = {r.rid: r.result for r in alone}
     levels = {}
     best = 0.0
-    for load in (0.5, 0.8, 0.95, 2.0, 5.0, 10.0, 20.0):
+    for load in (0.5, 0.8, 0.95, 2.0, 5.0, 10.0, 20.0, 50.0):
         rate = load * cap / mean
         arr, _, _ = W.workload_serving_requests(nreq, rate)
         srv = serve.Server(autos, hbm_budget=4 << 30, max_batch=256, slots=3)

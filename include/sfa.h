@@ -331,6 +331,86 @@ void sfa_batch_destroy(sfa_batch_t b);
 int sfa_match_batch(const sfa_handle_t *hs, const uint8_t *const *d_texts, const uint64_t *lens,
                     int32_t k, sfa_result *d_out, sfa_stream_t stream);
 
+/* ---- serving ------------------------------------------------------------- */
+/*
+ * A continuous-batching match server over resident automata (the paper has
+ * no counterpart: it is the serving loop around sfa_batch_*).  Requests are
+ * queued by sfa_server_submit; each sfa_server_progress call completes the
+ * batches the device has finished and admits queued requests, first in,
+ * first out, into free batch slots while the device text arena has room:
+ * their texts are copied into the arena (one cudaMemcpyAsync each) and
+ * matched by one persistent launch per batch on the slot's stream.  No call
+ * waits for the device, and nothing is allocated after sfa_server_create.
+ * Every result equals the text's result alone (sfa_match).  One thread at a
+ * time may call a server's functions.
+ */
+typedef struct sfa_server *sfa_server_t;
+
+typedef struct {
+    uint64_t hbm_budget;      /* device bytes of the text arena (0 = 4 GiB) */
+    int32_t max_batch;        /* requests per launch (0 = 256) */
+    int32_t slots;            /* batches in flight, one stream each (0 = 3) */
+    uint32_t chunk_bytes;     /* chunk length of the batch plans (0 = 1024) */
+    uint32_t block_threads;   /* CTA size of the batch plans (0 = 512) */
+} sfa_server_opts;
+
+typedef struct {
+    uint64_t tag;             /* the caller's tag of the request */
+    sfa_result result;
+} sfa_completion;
+
+typedef struct {
+    uint64_t queued;              /* submitted, not yet admitted */
+    uint64_t in_flight;           /* admitted, batch not yet finished */
+    uint64_t completed_waiting;   /* finished, not yet returned */
+    uint64_t batches;             /* launches so far */
+    uint64_t requests;            /* requests admitted so far */
+    uint64_t arena_used;          /* arena bytes held by admitted requests */
+} sfa_server_stats_t;
+
+/* sfa_server_create -- n automata (handles on the current device; the
+ * handles must outlive the server); opts NULL = defaults.  Allocates the
+ * arena, the batch plans, streams, events and pinned result buffers
+ * (synchronous).  Errors: INVALID, HOST_ONLY, NO_DEVICE, OOM, CUDA. */
+int sfa_server_create(const sfa_handle_t *automata, int32_t n, const sfa_server_opts *opts, sfa_server_t *out);
+
+/* sfa_server_submit -- queue one request: automaton index in [0, n), host
+ * text of len bytes (pinned for asynchronous copies; it must stay valid and
+ * unmodified until the request completes), and a tag returned with its
+ * result.  INVALID for a bad index, a NULL text with len > 0, or a text
+ * longer than the arena. */
+int sfa_server_submit(sfa_server_t s, int32_t automaton, const uint8_t *h_text, uint64_t len, uint64_t tag);
+
+/* sfa_server_submit_many -- k requests at once (arrays of automaton indices,
+ * host texts, lengths and tags, as for sfa_server_submit); all are queued,
+ * in order, or none (INVALID). */
+int sfa_server_submit_many(sfa_server_t s, int32_t k, const int32_t *automata, const uint8_t *const *h_texts,
+                           const uint64_t *lens, const uint64_t *tags);
+
+/* sfa_server_progress -- complete finished batches, admit and launch queued
+ * requests, and return up to cap completions in done[] (*n_done of them;
+ * the rest are kept for later calls).  A failure to enqueue a batch returns
+ * its error and leaves those requests at the head of the queue. */
+int sfa_server_progress(sfa_server_t s, sfa_completion *done, int32_t cap, int32_t *n_done);
+
+/* sfa_server_stats -- counters of the server's queue, slots and arena. */
+int sfa_server_stats(sfa_server_t s, sfa_server_stats_t *out);
+
+/* sfa_server_destroy -- waits for the slots' streams, then frees everything
+ * (NULL is fine).  Requests not yet completed are dropped. */
+void sfa_server_destroy(sfa_server_t s);
+
+/* The server's arena allocator, on its own (host only; offsets, no memory):
+ * first fit, ranges rounded up to 256 bytes, free neighbours merged.
+ * sfa_arena_alloc returns OOM when no free range is long enough;
+ * sfa_arena_release returns INVALID for a range that is not held. */
+typedef struct sfa_arena *sfa_arena_t;
+sfa_arena_t sfa_arena_create(uint64_t size);
+int sfa_arena_alloc(sfa_arena_t a, uint64_t n, uint64_t *off);
+int sfa_arena_release(sfa_arena_t a, uint64_t off, uint64_t n);
+uint64_t sfa_arena_used(sfa_arena_t a);
+void sfa_arena_destroy(sfa_arena_t a);
+
 /* ---- launch statistics (for benchmarks) --------------------------------- */
 /* Number of kernels the library enqueued since load (all entry points). */
 uint64_t sfa_kernel_launch_count(void);

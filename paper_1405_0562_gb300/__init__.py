@@ -40,6 +40,8 @@ EXPORTED = (
     "sfa_batch_create", "sfa_batch_launch", "sfa_batch_graph_launch", "sfa_batch_destroy",
     "sfa_match_batch", "sfa_kernel_launch_count", "sfa_match_noalloc",
     "sfa_batch_reserve", "sfa_batch_update", "sfa_batch_update_host",
+    "sfa_server_create", "sfa_server_submit", "sfa_server_submit_many", "sfa_server_progress", "sfa_server_stats", "sfa_server_destroy",
+    "sfa_arena_create", "sfa_arena_alloc", "sfa_arena_release", "sfa_arena_used", "sfa_arena_destroy",
 )
 
 
@@ -74,6 +76,21 @@ class LaunchOpts(ctypes.Structure):
 class Result(ctypes.Structure):
     _fields_ = [("final_state", ctypes.c_uint32), ("accept_final", ctypes.c_uint8),
                 ("status", ctypes.c_uint8), ("reserved", ctypes.c_uint16), ("count", ctypes.c_uint64)]
+
+
+class ServerOpts(ctypes.Structure):
+    _fields_ = [("hbm_budget", ctypes.c_uint64), ("max_batch", ctypes.c_int32), ("slots", ctypes.c_int32),
+                ("chunk_bytes", ctypes.c_uint32), ("block_threads", ctypes.c_uint32)]
+
+
+class Completion(ctypes.Structure):
+    _fields_ = [("tag", ctypes.c_uint64), ("result", Result)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("queued", ctypes.c_uint64), ("in_flight", ctypes.c_uint64),
+                ("completed_waiting", ctypes.c_uint64), ("batches", ctypes.c_uint64),
+                ("requests", ctypes.c_uint64), ("arena_used", ctypes.c_uint64)]
 
 
 _lib_handle = None
@@ -111,8 +128,24 @@ def lib():
     L.sfa_batch_reserve.argtypes = [i32, u64, u32, ctypes.POINTER(LaunchOpts), ctypes.POINTER(P)]
     L.sfa_batch_update.argtypes = [P, P, P, P, i32, P]
     L.sfa_batch_update_host.argtypes = [P, P, P, P, P, i32, P]
+    L.sfa_server_create.argtypes = [P, i32, ctypes.POINTER(ServerOpts), ctypes.POINTER(P)]
+    L.sfa_server_submit.argtypes = [P, i32, P, u64, u64]
+    L.sfa_server_submit_many.argtypes = [P, i32, P, P, P, P]
+    L.sfa_server_progress.argtypes = [P, ctypes.POINTER(Completion), i32, ctypes.POINTER(i32)]
+    L.sfa_server_stats.argtypes = [P, ctypes.POINTER(ServerStats)]
+    L.sfa_server_destroy.argtypes = [P]
+    L.sfa_server_destroy.restype = None
+    L.sfa_arena_create.argtypes = [u64]
+    L.sfa_arena_create.restype = P
+    L.sfa_arena_alloc.argtypes = [P, u64, ctypes.POINTER(u64)]
+    L.sfa_arena_release.argtypes = [P, u64, u64]
+    L.sfa_arena_used.argtypes = [P]
+    L.sfa_arena_used.restype = u64
+    L.sfa_arena_destroy.argtypes = [P]
+    L.sfa_arena_destroy.restype = None
     for name in EXPORTED:
-        if name not in ("sfa_destroy", "sfa_batch_destroy", "sfa_strerror", "sfa_kernel_launch_count"):
+        if name not in ("sfa_destroy", "sfa_batch_destroy", "sfa_strerror", "sfa_kernel_launch_count",
+                        "sfa_server_destroy", "sfa_arena_create", "sfa_arena_used", "sfa_arena_destroy"):
             getattr(L, name).restype = ctypes.c_int
     _lib_handle = L
     return L

@@ -3,67 +3,59 @@
 Requests (automaton index, host text) arrive over time.  The server keeps
 every compiled automaton resident on the device, admits requests while its
 HBM text budget and the batch capacity allow, copies the admitted texts into
-a device arena and matches them in one persistent launch per batch
-(``sfa_batch_update`` + ``sfa_batch_launch``: no allocation, no host
-synchronisation on the launch path).  Several batch slots, each on its own
-CUDA stream, are in flight at once: requests that arrive while a batch runs
-are admitted into the next free slot as soon as memory frees up, so their
-copies and kernels overlap the running batch.  Completion is detected by
-polling CUDA events; each request's latency is completion time minus arrival
-time on the host clock.
+a device arena and matches them in one persistent launch per batch.  The
+loop itself is native (``sfa_server_*`` in the C ABI): the queue, the arena
+allocator, the batch slots (each on its own CUDA stream, several in flight)
+and the completion polling by CUDA events run in C++, one cudaMemcpyAsync
+per request and one launch per batch, with no allocation and no host wait on
+the launch path.  This module drives it: it submits requests at their
+arrival times, collects completions and stamps each request's latency
+(completion time minus arrival time on the host clock).
 
 Every result equals the result of matching the text alone (each text has
 its own look-back chain and record in the batch kernel).
 """
 from __future__ import annotations
 
-import bisect
 import ctypes
 import dataclasses
 import time
-from collections import deque
-from typing import List, Optional, Sequence
+from typing import Dict, List, Optional, Sequence
 
 import numpy as np
 
-from . import (Automaton, LaunchOpts, RESULT_BYTES, _check, _stream_ptr, decode, lib)
+from . import (Automaton, Completion, RESULT_BYTES, ServerOpts, ServerStats, _check, decode, lib)
 
 _ALIGN = 256
 
 
 class ArenaAllocator:
-    """First-fit allocator of byte ranges in a fixed device arena (offsets
-    only; the memory is one tensor).  Ranges are 256-byte aligned."""
+    """The server's first-fit allocator of byte ranges in a fixed arena
+    (offsets only), ranges 256-byte aligned, free neighbours merged: the
+    native one, usable on its own (no device needed)."""
 
     def __init__(self, size: int):
         self.size = size
-        self.free: List[List[int]] = [[0, size]]   # sorted [start, end)
-        self.used = 0
+        self._a = lib().sfa_arena_create(size)
+        if not self._a:
+            raise MemoryError("sfa_arena_create")
 
     def alloc(self, n: int) -> Optional[int]:
-        n = max(_ALIGN, (n + _ALIGN - 1) // _ALIGN * _ALIGN)
-        for i, (s, e) in enumerate(self.free):
-            if e - s >= n:
-                if e - s == n:
-                    self.free.pop(i)
-                else:
-                    self.free[i][0] = s + n
-                self.used += n
-                return s
-        return None
+        off = ctypes.c_uint64()
+        rc = lib().sfa_arena_alloc(self._a, n, ctypes.byref(off))
+        return int(off.value) if rc == 0 else None
 
     def release(self, off: int, n: int):
-        n = max(_ALIGN, (n + _ALIGN - 1) // _ALIGN * _ALIGN)
-        self.used -= n
-        i = bisect.bisect_left(self.free, [off, off + n])
-        self.free.insert(i, [off, off + n])
-        # merge with neighbours
-        if i + 1 < len(self.free) and self.free[i][1] == self.free[i + 1][0]:
-            self.free[i][1] = self.free[i + 1][1]
-            self.free.pop(i + 1)
-        if i > 0 and self.free[i - 1][1] == self.free[i][0]:
-            self.free[i - 1][1] = self.free[i][1]
-            self.free.pop(i)
+        _check(lib().sfa_arena_release(self._a, off, n), "sfa_arena_release")
+
+    @property
+    def used(self) -> int:
+        return int(lib().sfa_arena_used(self._a))
+
+    def __del__(self):
+        if getattr(self, "_a", None):
+            lib().sfa_arena_destroy(self._a)
+            self._a = None
 
 
 @dataclasses.dataclass
@@ -95,137 +87,117 @@ def _host_ptr(text) -> int:
     return a.ctypes.data if a.size else 0
 
 
-class _Slot:
-    def __init__(self, torch, max_texts, max_tiles, nr_max, opts, device):
-        self.stream = torch.cuda.Stream(device=device)
-        self.out = torch.zeros(max_texts * RESULT_BYTES, dtype=torch.uint8, device=device)
-        self.out_host = torch.zeros(max_texts * RESULT_BYTES, dtype=torch.uint8).pin_memory()
-        self.event = torch.cuda.Event()
-        self.reqs: List[Request] = []
-        b = ctypes.c_void_p()
-        _check(lib().sfa_batch_reserve(max_texts, max_tiles, nr_max, ctypes.byref(opts), ctypes.byref(b)),
-               "sfa_batch_reserve")
-        self.plan = b
-
-    def close(self):
-        if self.plan is not None and self.plan.value:
-            lib().sfa_batch_destroy(self.plan)
-            self.plan = None
-
-
 class Server:
-    """Continuous batching over resident automata with HBM-budget admission."""
+    """Continuous batching over resident automata with HBM-budget admission
+    (the native server, driven from Python)."""
 
-    def __init__(self, automata: Sequence[Automaton], hbm_budget: int = 4 << 30, max_batch: int = 512,
+    def __init__(self, automata: Sequence[Automaton], hbm_budget: int = 4 << 30, max_batch: int = 256,
                  slots: int = 3, chunk_bytes: int = 1024, block_threads: int = 512, device=None):
         import torch
-        self.torch = torch
-        self.device = device or torch.device("cuda", torch.cuda.current_device())
+        if device is not None:
+            torch.cuda.set_device(device)
         self.automata = list(automata)
-        nr_max = max(a.info()["n_reachable"] for a in self.automata)
-        self.arena = torch.empty(hbm_budget, dtype=torch.uint8, device=self.device)
-        self.alloc = ArenaAllocator(hbm_budget)
-        self.max_batch = max_batch
-        self.opts = LaunchOpts(chunk_bytes, block_threads, 1, 0, 0, 0, 0, 0)
-        cpt = block_threads
-        max_tiles = max_batch + hbm_budget // (cpt * chunk_bytes) + 1
-        self.slots = [_Slot(torch, max_batch, max_tiles, nr_max, self.opts, self.device) for _ in range(slots)]
-        self.free_slots = deque(self.slots)
-        self.busy: List[_Slot] = []
-        self.queue: deque = deque()
+        hs = (ctypes.c_void_p * len(self.automata))(*[a.handle.value for a in self.automata])
+        opts = ServerOpts(hbm_budget, max_batch, slots, chunk_bytes, block_threads)
+        s = ctypes.c_void_p()
+        _check(lib().sfa_server_create(hs, len(self.automata), ctypes.byref(opts), ctypes.byref(s)),
+               "sfa_server_create")
+        self._s = s
+        self.budget = hbm_budget
+        self._pending: Dict[int, Request] = {}
+        self._cap = 4096
+        self._buf = (Completion * self._cap)()
+        self._n = ctypes.c_int32()
         self.completed: List[Request] = []
-        self.batches = 0
-        self.batched_requests = 0
 
     # ---- request flow ----------------------------------------------------
     def submit(self, req: Request):
-        if req.nbytes > self.alloc.size:
+        if req.nbytes > self.budget:
             raise ValueError("request larger than the HBM text budget")
-        self.queue.append(req)
-
-    def poll(self):
-        """Complete every slot whose batch has finished."""
-        still = []
-        for s in self.busy:
-            if s.event.query():
-                now = time.perf_counter()
-                res = decode(s.out_host[:len(s.reqs) * RESULT_BYTES])
-                for r, x in zip(s.reqs, res):
-                    r.result = x
-                    r.done = now
-                    self.alloc.release(r.offset, r.nbytes)
-                    self.completed.append(r)
-                s.reqs = []
-                self.free_slots.append(s)
-            else:
-                still.append(s)
-        self.busy = still
-
-    def admit_and_launch(self):
-        """Fill free slots from the queue (FIFO, while memory allows) and
-        launch them."""
-        torch = self.torch
-        while self.free_slots and self.queue:
-            slot = self.free_slots[0]
-            take: List[Request] = []
-            while self.queue and len(take) < self.max_batch:
-                r = self.queue[0]
-                off = self.alloc.alloc(r.nbytes)
-                if off is None:
-                    break
-                r.offset = off
-                take.append(self.queue.popleft())
-            if not take:
-                return
-            self.free_slots.popleft()
-            now = time.perf_counter()
-            k = len(take)
-            hs = (ctypes.c_void_p * k)(*[self.automata[r.automaton].handle.value for r in take])
-            base = self.arena.data_ptr()
-            ptrs = (ctypes.c_void_p * k)(*[base + r.offset for r in take])
-            lens = (ctypes.c_uint64 * k)(*[r.nbytes for r in take])
-            srcs = (ctypes.c_void_p * k)(*[_host_ptr(r.text) for r in take])
-            for r in take:
-                r.admitted = now
-            with torch.cuda.stream(slot.stream):
-                sp = _stream_ptr(slot.stream)
-                # copies of the texts into the arena and the new work list,
-                # enqueued natively on the slot's stream
-                _check(lib().sfa_batch_update_host(slot.plan, hs, srcs, ptrs, lens, k, sp), "sfa_batch_update_host")
-                _check(lib().sfa_batch_launch(slot.plan, slot.out.data_ptr(), sp), "sfa_batch_launch")
-                slot.out_host[:k * RESULT_BYTES].copy_(slot.out[:k * RESULT_BYTES], non_blocking=True)
-                slot.event.record(slot.stream)
-            slot.reqs = take
-            self.busy.append(slot)
-            self.batches += 1
-            self.batched_requests += k
+        if req.rid in self._pending:
+            raise ValueError("request id already in flight")
+        self._pending[req.rid] = req
+        _check(lib().sfa_server_submit(self._s, req.automaton, _host_ptr(req.text), req.nbytes, req.rid),
+               "sfa_server_submit")
 
     def step(self):
-        self.poll()
-        self.admit_and_launch()
+        """Complete finished batches, admit and launch queued requests."""
+        L = lib()
+        while True:
+            _check(L.sfa_server_progress(self._s, self._buf, self._cap, ctypes.byref(self._n)),
+                   "sfa_server_progress")
+            k = self._n.value
+            if not k:
+                return
+            now = time.perf_counter()
+            raw = np.ctypeslib.as_array(ctypes.cast(self._buf, ctypes.POINTER(ctypes.c_uint64)),
+                                        shape=(k * 3,)).reshape(k, 3)
+            res = decode(raw[:, 1:].copy().view(np.uint8))
+            for tag, x in zip(raw[:, 0].tolist(), res):
+                r = self._pending.pop(tag)
+                r.result = x
+                r.done = now
+                self.completed.append(r)
+            if k < self._cap:
+                return
+
+    poll = step
+
+    def stats(self) -> dict:
+        """Queue, slot and arena counters (the last ones once closed)."""
+        if getattr(self, "_s", None) is None:
+            return dict(self._final)
+        st = ServerStats()
+        _check(lib().sfa_server_stats(self._s, ctypes.byref(st)), "sfa_server_stats")
+        return {f: int(getattr(st, f)) for f, _ in ServerStats._fields_}
+
+    @property
+    def batches(self) -> int:
+        return self.stats()["batches"]
 
     def idle(self) -> bool:
-        return not self.queue and not self.busy
+        return not self._pending
 
     def close(self):
-        for s in self.slots:
-            s.close()
+        if getattr(self, "_s", None) is not None and self._s.value:
+            self._final = self.stats()
+            lib().sfa_server_destroy(self._s)
+            self._s = None
+
+    def __del__(self):
+        self.close()
 
     # ---- driving a workload ------------------------------------------------
     def run(self, requests: Sequence[Request], realtime: bool = True):
         """Submit each request at its arrival time (offsets from now) and
-        serve until all are done.  Returns the completed requests."""
-        t0 = time.perf_counter()
+        serve until all are done.  Returns the completed requests.  The
+        requests' arrays (automaton, text address, length, id) are built
+        before the clock starts; the requests due at each turn of the loop
+        go to the server in one call."""
         pending = sorted(requests, key=lambda r: r.arrival)
-        rel = [r.arrival for r in pending]
+        n = len(pending)
+        for r in pending:
+            if r.nbytes > self.budget:
+                raise ValueError("request larger than the HBM text budget")
+            if r.rid in self._pending:
+                raise ValueError("request id already in flight")
+        rel = np.array([r.arrival for r in pending], dtype=np.float64)
+        auto = np.array([r.automaton for r in pending], dtype=np.int32)
+        ptr = np.array([_host_ptr(r.text) for r in pending], dtype=np.uint64)
+        ln = np.array([r.nbytes for r in pending], dtype=np.uint64)
+        tag = np.array([r.rid for r in pending], dtype=np.uint64)
+        L = lib()
+        t0 = time.perf_counter()
         i = 0
-        while i < len(pending) or not self.idle():
-            now = time.perf_counter() - t0
-            while i < len(pending) and (not realtime or rel[i] <= now):
-                r = pending[i]
-                r.arrival = t0 + rel[i]
-                self.submit(r)
-                i += 1
+        while i < n or not self.idle():
+            j = n if not realtime else int(np.searchsorted(rel, time.perf_counter() - t0, side="right"))
+            if j > i:
+                for r, a in zip(pending[i:j], rel[i:j].tolist()):
+                    r.arrival = t0 + a
+                    self._pending[r.rid] = r
+                _check(L.sfa_server_submit_many(self._s, j - i, auto[i:].ctypes.data, ptr[i:].ctypes.data,
+                                                ln[i:].ctypes.data, tag[i:].ctypes.data), "sfa_server_submit_many")
+                i = j
             self.step()
         return self.completed
 

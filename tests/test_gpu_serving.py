@@ -155,3 +155,15 @@ def test_server_results_equal_alone(sfa):
     by_id = {r.rid: r.result for r in done}
     for r in alone:
         assert r.result == by_id[r.rid]
+    # a 3 MiB arena and small batches: admission waits for memory, every
+    # request still completes with the same result
+    srv = serve.Server(autos, hbm_budget=3 << 20, max_batch=8, slots=2)
+    try:
+        again = srv.run([serve.Request(r.rid, r.automaton, r.text, 0.0) for r in done], realtime=False)
+        st = srv.stats()
+    finally:
+        srv.close()
+    assert len(again) == len(done) and st["queued"] == 0 and st["in_flight"] == 0 and st["arena_used"] == 0
+    assert st["requests"] == len(done) and st["batches"] >= len(done) // 8
+    for r in again:
+        assert r.result == by_id[r.rid], r.rid
