@@ -521,6 +521,78 @@ def run_serving(args, rank, world, local):
         print(json.dumps(line), flush=True)
 
 
+def run_crossover(args, rank, world, local):
+    """Small-input crossover (the paper's Sect. VI-C study, on a GPU): per text
+    length, the latency of one match on the device (a CUDA graph of the
+    call, replayed), end to end from pinned host memory (sfa_match_host:
+    copy in, match, copy the result back, synchronise), and the oracle's
+    sequential Alg. 2 on one host core; the crossover is the shortest text
+    the GPU matches end to end faster than the CPU."""
+    import ctypes
+
+    import torch
+
+    import oracle
+    import paper_1405_0562_gb300 as sfa
+    torch.cuda.set_device(local)
+    d, t = W.workload_large(64 << 20)
+    a = sfa.Automaton.from_dfa(d)
+    stream = torch.cuda.Stream()
+    dl, al = oracle._dfa_arrays(d.delta, d.accept)
+    lib = oracle._lib()
+    cnt = np.zeros(1, dtype=np.uint64)
+    rows = []
+    for n in (1 << 10, 4 << 10, 16 << 10, 64 << 10, 256 << 10, 1 << 20, 4 << 20, 16 << 20, 64 << 20):
+        tt = torch.from_numpy(t[:n]).cuda()
+        pinned = torch.from_numpy(t[:n]).pin_memory()
+        out = sfa.empty_results(1)
+        with torch.cuda.stream(stream):
+            for _ in range(3):
+                a.match(tt, out, stream=stream)
+        stream.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=stream):
+            a.match(tt, out, stream=stream)
+        reps = 200
+        with torch.cuda.stream(stream):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                g.replay()
+            e1.record(stream)
+        stream.synchronize()
+        dev_us = e0.elapsed_time(e1) / reps * 1e3
+        got = sfa.decode(out)[0]
+        a.match_host(pinned, stream=stream)
+        k = 50
+        t0 = time.perf_counter()
+        for _ in range(k):
+            res = a.match_host(pinned, stream=stream)
+        e2e_us = (time.perf_counter() - t0) / k * 1e6
+        tp = t[:n]
+        k = max(3, int(2e7 // max(n, 1)))
+        t0 = time.perf_counter()
+        for _ in range(k):
+            f = lib.oracle_dfa_run(oracle._ptr(dl), dl.shape[0], int(d.q0), oracle._ptr(al), oracle._ptr(tp), n,
+                                   oracle._ptr(cnt))
+        cpu_us = (time.perf_counter() - t0) / k * 1e6
+        want = (int(f), int(al[f]), 0, int(cnt[0]))
+        assert got == want and res == want, (n, got, res, want)
+        rows.append({"bytes": n, "gpu_device_us": dev_us, "gpu_e2e_us": e2e_us, "cpu_oracle_us": cpu_us})
+    cross = next((r["bytes"] for r in rows if r["gpu_e2e_us"] < r["cpu_oracle_us"]), None)
+    big = rows[-1]
+    line = {"metric": METRIC, "value": big["bytes"] / (big["gpu_device_us"] * 1e-6) / 1e9, "unit": "GB/s",
+            "n_gpus": world, "steps": len(rows), "warmup": 3, "ms_per_step": None, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "config": {"workload": "crossover: prefixes (1 KiB .. 64 MiB) of the 1 GiB Aho-Corasick/Zipf text, "
+                                   "one match at a time", "seed": W.SEED_LARGE},
+            "rows": rows, "crossover_bytes_e2e": cross,
+            "cpu_baseline": {"value": big["bytes"] / (big["cpu_oracle_us"] * 1e-6) / 1e9, "unit": "GB/s",
+                             "cores": 1, "kind": "oracle", "sample": "each prefix, repeated to about 20 MB"}}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -528,7 +600,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--workload", default="plain_large",
-                    choices=["plain_large", "plain_small", "batched", "sim", "serving"])
+                    choices=["plain_large", "plain_small", "batched", "sim", "serving", "crossover"])
     ap.add_argument("--requests", type=int, default=20000, help="serving: requests per offered load")
     ap.add_argument("--check", action="store_true", help="sim: compare the full outputs with the oracle")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -546,6 +618,8 @@ def main():
         run_sim(args, rank, world, local)
     elif args.workload == "serving":
         run_serving(args, rank, world, local)
+    elif args.workload == "crossover":
+        run_crossover(args, rank, world, local)
     else:
         run_gpu(args, rank, world, local)
     if world > 1:
