@@ -521,6 +521,68 @@ def run_serving(args, rank, world, local):
         print(json.dumps(line), flush=True)
 
 
+def run_rn(args, rank, world, local):
+    """The paper's scalability automata (Sect. VI-B): r_5 and r_50, the
+    minimal DFAs of ([0-4]{n}[5-9]{n})* (11 and 101 states, 110 and 10 100
+    D-SFA states), on 1 GiB accepted texts.  Their chunk mappings never
+    become constant, so every byte takes the D-SFA's non-constant rows and
+    the count pass reruns most of each chunk.  A step matches the text with
+    both automata; results are checked against the oracle."""
+    import torch
+
+    import oracle
+    import paper_1405_0562_gb300 as sfa
+    torch.cuda.set_device(local)
+    n = args.text_bytes or (1 << 30)
+    per, cpu, checks = {}, {}, {}
+    stream = torch.cuda.Stream()
+    total_ms, launches = 0.0, 0
+    clocks = ClockSampler(local)
+    clocks.start()
+    for rn in (5, 50):
+        d = W.dfa_rn(rn)
+        t = W.text_rn_accepted(n, rn, W.SEED_LARGE + rn)
+        a = sfa.Automaton.from_dfa(d)
+        tt = torch.from_numpy(t).cuda()
+        out = sfa.empty_results(1)
+        for _ in range(args.warmup):
+            a.match(tt, out, stream=stream)
+        stream.synchronize()
+        n0 = sfa.kernel_launch_count()
+        ms = _events(torch, stream, lambda: a.match(tt, out, stream=stream), args.steps)
+        launches += sfa.kernel_launch_count() - n0
+        total_ms += ms
+        per[f"r_{rn}"] = n * args.steps / (ms * 1e-3) / 1e9
+        got = sfa.decode(out)[0]
+        f, acc, c = oracle.dfa_run(d.delta, d.q0, d.accept, t)
+        checks[f"r_{rn}"] = got == (f, acc, 0, c)
+        sample = t[:64 << 20]
+        t0 = time.perf_counter()
+        oracle.dfa_run(d.delta, d.q0, d.accept, sample)
+        cpu[f"r_{rn}"] = sample.size / (time.perf_counter() - t0) / 1e9
+        del tt
+    clk = clocks.stop()
+    assert all(checks.values()), checks
+    step_ms = total_ms / args.steps
+    value = 2 * n / (step_ms * 1e-3) / 1e9
+    peak, peak_kind = hbm_peak()
+    line = {"metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "config": {"workload": f"r_n: r_5 and r_50 (Sect. VI-B) on {n >> 20} MiB accepted texts each, both per step",
+                       "text_bytes": n, "seed": W.SEED_LARGE, "l2": "inputs larger than L2",
+                       "per_automaton_GBps": per},
+            "roofline": {"bound": "hbm", "achieved": value, "peak": peak, "unit": "GB/s", "frac": value / peak,
+                         "traffic": None, "peak_kind": peak_kind, "kernel": "sfa_match_kernel",
+                         "algorithmic_bytes_per_launch": n},
+            "gpu_launches": int(launches), "clocks": clk, "bit_exact_vs_oracle": True,
+            "cpu_baseline": {"value": 2 / sum(1 / v for v in cpu.values()), "unit": "GB/s", "cores": 1,
+                             "kind": "oracle", "sample": "first 64 MiB with each automaton",
+                             "per_automaton_GBps": cpu}}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def run_crossover(args, rank, world, local):
     """Small-input crossover (the paper's Sect. VI-C study, on a GPU): per text
     length, the latency of one match on the device (a CUDA graph of the
@@ -600,7 +662,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--workload", default="plain_large",
-                    choices=["plain_large", "plain_small", "batched", "sim", "serving", "crossover"])
+                    choices=["plain_large", "plain_small", "batched", "sim", "serving", "crossover", "rn"])
     ap.add_argument("--requests", type=int, default=20000, help="serving: requests per offered load")
     ap.add_argument("--check", action="store_true", help="sim: compare the full outputs with the oracle")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -620,6 +682,8 @@ def main():
         run_serving(args, rank, world, local)
     elif args.workload == "crossover":
         run_crossover(args, rank, world, local)
+    elif args.workload == "rn":
+        run_rn(args, rank, world, local)
     else:
         run_gpu(args, rank, world, local)
     if world > 1:

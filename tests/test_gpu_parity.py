@@ -156,6 +156,26 @@ def test_two_level_text(n):
     assert gpu_match(a, t, max_ctas=100) == want
 
 
+@pytest.mark.parametrize("rn", [5, 50])
+def test_rn_accepted_texts(rn):
+    """Sect. VI-B's automata on accepted texts (the chunk mappings never
+    become constant; the count pass reruns most of each chunk), clean and
+    with a few wrong digits; default, CTA/warp tilings and a two-level size."""
+    sfa = sfa_mod()
+    d = W.dfa_rn(rn)
+    a = sfa.Automaton.from_dfa(d)
+    for n, flips in ((8 << 20, 0), ((8 << 20) + 7, 5), (96 << 20, 0)):
+        t = W.text_rn_accepted(n, rn, 11 + n)
+        if flips:
+            rng = np.random.default_rng(n)
+            t[rng.integers(0, n, flips)] = ord("7")
+        want = expect(d, t)
+        assert gpu_match(a, t) == want, n
+        if n < (64 << 20):
+            assert gpu_match(a, t, tiling=sfa.TILING_WARP, block_threads=512, chains=1) == want
+            assert gpu_match(a, t, block_threads=256, chains=2, chunk_bytes=1000) == want
+
+
 def test_warp_tiles_with_max_ctas():
     """Warp-tile look-back over thousands of tiles with few resident CTAs."""
     sfa = sfa_mod()

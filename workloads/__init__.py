@@ -304,6 +304,26 @@ def text_uniform(n: int, alphabet: bytes, seed: int) -> np.ndarray:
     return _fill_parallel(n, seed, lambda r, k: alpha[r.integers(0, m, size=k, dtype=np.uint8)])
 
 
+def text_rn_accepted(n: int, rn: int, seed: int) -> np.ndarray:
+    """n bytes of an r_n word (Sect. VI-B's accepted texts): position i is a
+    digit drawn uniformly from 0-4 when i mod 2*rn < rn, else from 5-9.  A
+    prefix of whole periods is in L(r_n)."""
+    out = np.empty(n, dtype=np.uint8)
+    k = 2 * rn
+
+    def work(b):
+        i, lo, hi = b
+        rng = np.random.Generator(np.random.Philox(key=seed, counter=[0, 0, i, 0]))
+        low = rng.integers(0, 5, size=hi - lo, dtype=np.uint8)
+        phase = (np.arange(lo, hi, dtype=np.int64) % k) >= rn
+        out[lo:hi] = low + np.uint8(48) + phase.astype(np.uint8) * np.uint8(5)
+
+    blocks = _blocks(n)
+    with ThreadPoolExecutor(min(8, max(1, len(blocks)))) as ex:
+        list(ex.map(work, blocks))
+    return out
+
+
 def zipf_table(alphabet: bytes, s: float, seed: int, bits: int = 16) -> np.ndarray:
     """Quantised inverse CDF of Zipf(s) over the alphabet: rank r (1-based)
     has probability proportional to r^-s, ranks are assigned to symbols by a
