@@ -178,13 +178,12 @@ __device__ __forceinline__ void sfa_step(Chain &s, uint32_t b, int32_t j, const 
     if (s.f >= nr) {
         const uint32_t e = __ldg(nc + (size_t)(s.f - nr) * ncls + s_cls[b]);
         s.f = e & NC_ID_MASK;
+        // the class bits, without divergent branches
         const uint32_t a = e >> 30;
-        if (a == ACC_ALL) {
-            s.cnt++;
-        } else if (a == ACC_MIXED) {
-            s.lm = j;
-            s.snap = s.cnt;
-        }
+        const bool mixed = a == ACC_MIXED;
+        s.cnt += a == ACC_ALL;
+        s.lm = mixed ? j : s.lm;
+        s.snap = mixed ? s.cnt : s.snap;
     } else {
         s.f = s_dfa[didx(s.f, b)];
         s.cnt += s.f >= first_accept;
@@ -372,13 +371,28 @@ __device__ __forceinline__ uint32_t dfa_count(const uint8_t *text, uint64_t p, u
         c += q >= first_accept;
         ++p;
     }
-    for (; p + 16 <= e; p += 16) {
-        const uint4 v = ldg128(text + p);
+    // 16-byte words, the next two loaded while the current two are counted
+    // (a long rerun reads its text from HBM)
+    auto word16 = [&](const uint4 &v) {
         dfa_word(q, c, v.x, s_dfa, first_accept);
         dfa_word(q, c, v.y, s_dfa, first_accept);
         dfa_word(q, c, v.z, s_dfa, first_accept);
         dfa_word(q, c, v.w, s_dfa, first_accept);
+    };
+    if (p + 32 <= e) {
+        uint4 v0 = ldg128(text + p), v1 = ldg128(text + p + 16);
+        for (; p + 64 <= e; p += 32) {
+            const uint4 n0 = ldg128(text + p + 32), n1 = ldg128(text + p + 48);
+            word16(v0);
+            word16(v1);
+            v0 = n0;
+            v1 = n1;
+        }
+        word16(v0);
+        word16(v1);
+        p += 32;
     }
+    for (; p + 16 <= e; p += 16) word16(ldg128(text + p));
     for (; p < e; ++p) {
         q = s_dfa[didx(q, text[p])];
         c += q >= first_accept;
