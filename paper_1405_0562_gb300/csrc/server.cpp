@@ -171,6 +171,17 @@ int server_admit(sfa_server *s) {
         int rc = sfa_batch_update_host(sl.plan, s->hs.data(), s->src.data(), s->dst.data(), s->lens.data(), k,
                                        sl.stream);
         if (!rc) rc = sfa_batch_launch(sl.plan, sl.d_out, sl.stream);
+        if (!rc) {
+            cudaError_t e = cudaMemcpyAsync(sl.h_out, sl.d_out, (size_t)k * sizeof(sfa_result),
+                                            cudaMemcpyDeviceToHost, sl.stream);
+            if (e == cudaSuccess) e = cudaEventRecord(sl.ev, sl.stream);
+            if (e != cudaSuccess) {
+                // the batch may still run, but its completion cannot be
+                // observed: wait for the stream before the arena is reused
+                cudaStreamSynchronize(sl.stream);
+                rc = sfa_impl::cuda_err(e);
+            }
+        }
         if (rc) {
             // put the requests back at the head of the queue, in order
             for (int32_t i = k - 1; i >= 0; --i) {
@@ -180,8 +191,6 @@ int server_admit(sfa_server *s) {
             sl.reqs.clear();
             return rc;
         }
-        CK(cudaMemcpyAsync(sl.h_out, sl.d_out, (size_t)k * sizeof(sfa_result), cudaMemcpyDeviceToHost, sl.stream));
-        CK(cudaEventRecord(sl.ev, sl.stream));
         sl.busy = true;
         ++s->batches;
         s->requests += (uint64_t)k;
