@@ -140,18 +140,33 @@ static __device__ __noinline__ uint64_t wait_descriptor(const uint64_t *p, uint3
 }
 
 // Bounded wait for the completion of an mbarrier phase (a stage of bulk
-// copies).  On giving up (timeout_us, or 2^24 polls) it raises the launch
-// error and returns; the stage's bytes are then not trusted.
+// copies).  Gives up after timeout_us or 2^24 polls, or soon after another
+// wait of the launch gave up; on giving up it raises the launch error and
+// returns (the stage's bytes are then not trusted, the results flagged).
 static __device__ __noinline__ void wait_stage_slow(uint32_t bar, uint32_t parity, uint32_t *err,
                                                     uint32_t timeout_us) {
     const uint64_t t0 = globaltimer();
     const uint64_t limit = (uint64_t)timeout_us * 1000ull;
     for (uint32_t it = 1;; ++it) {
         if (mbar_try_wait(bar, parity)) return;
-        if ((it & 63u) == 0 && (globaltimer() - t0 > limit || it > (1u << 24))) {
+        if ((it & 63u) == 0 &&
+            (*(volatile uint32_t *)err || globaltimer() - t0 > limit || it > (1u << 24))) {
             atomicOr(err, 1u);
             return;
         }
+    }
+}
+
+// After a launch error: before a warp leaves, a bounded wait for the last
+// phase of each of its stages (the one a wait may have given up on), so that
+// its bulk copies do not land in shared memory after the CTA has exited.
+static __device__ __noinline__ void drain_stages(uint32_t bar0, uint32_t parity, int stages, uint32_t timeout_us) {
+    const uint64_t limit = (uint64_t)timeout_us * 1000ull;
+    for (int st = 0; st < stages; ++st) {
+        const uint32_t last = ((parity >> st) & 1u) ^ 1u;
+        const uint64_t t0 = globaltimer();
+        for (uint32_t it = 1; !mbar_try_wait(bar0 + 8 * st, last); ++it)
+            if ((it & 63u) == 0 && (globaltimer() - t0 > limit || it > (1u << 24))) break;
     }
 }
 __device__ __forceinline__ void wait_stage(uint32_t bar, uint32_t parity, uint32_t *err, uint32_t timeout_us) {
@@ -619,6 +634,7 @@ __global__ void __launch_bounds__(THREADS, (min_ctas_per_sm<THREADS, CH, SIMNQ, 
             // staging the tables (the one CTA barrier of the launch)
             if (WT && loaded != 0u) stage_tables(tab, 0u);
             if (DEFER && tid == 0 && s_misc->dfr_valid) resolve_deferred<BATCH>(s_misc, S, tab, desc, tabs, descs, out);
+            if (*(volatile uint32_t *)&S.hdr->err) drain_stages(bar0, parity, STAGES, S.timeout_us);
             break;
         }
 
@@ -992,7 +1008,10 @@ __global__ void __launch_bounds__(THREADS, (min_ctas_per_sm<THREADS, CH, SIMNQ, 
             if (lane == 0) finish_tile(S, T, d, ts, out, tsum, local, incl);
             __syncwarp();
             // every warp of the grid had at most one tile: no second grab
-            if (!BATCH && S.total_tiles <= gridDim.x * (uint32_t)NW) break;
+            if (!BATCH && S.total_tiles <= gridDim.x * (uint32_t)NW) {
+                if (*(volatile uint32_t *)&S.hdr->err) drain_stages(bar0, parity, STAGES, S.timeout_us);
+                break;
+            }
             continue;
         }
 
@@ -1140,7 +1159,10 @@ __global__ void __launch_bounds__(THREADS, (min_ctas_per_sm<THREADS, CH, SIMNQ, 
         __syncthreads();
         // every CTA of the grid had at most one tile (each CTA takes one
         // per grab): no second grab
-        if (!BATCH && S.total_tiles <= gridDim.x) break;
+        if (!BATCH && S.total_tiles <= gridDim.x) {
+            if (*(volatile uint32_t *)&S.hdr->err) drain_stages(bar0, parity, STAGES, S.timeout_us);
+            break;
+        }
     }
 }
 
