@@ -70,6 +70,7 @@ uint64_t text_chunk(uint64_t n, uint64_t chunk, uint64_t cpt) {
     return std::min<uint64_t>(chunk, std::max<uint64_t>(64, align_up((n + cpt - 1) / cpt, 16)));
 }
 
+// (an upper bound for any origin: an origin never adds a chunk)
 uint64_t text_tiles(uint64_t n, uint64_t chunk, uint64_t cpt) {
     TextDesc d{};
     d.n = n;
@@ -130,6 +131,7 @@ int fill_worklist(sfa_batch *b, const sfa_handle_t *hs, const uint8_t *const *d_
         d.n = lens[i];
         d.chunk = text_chunk(d.n, b->chunk, cpt);
         d.forced = 0;
+        d.origin = sfa_dev::text_origin(d.text);
         if (sfa_dev::num_chunks(d) >= (1ull << 31)) return SFA_ERR_INVALID;
         const uint64_t t = (sfa_dev::num_chunks(d) + cpt - 1) / cpt;
         if (tiles + t > b->cap_tiles) return SFA_ERR_INVALID;

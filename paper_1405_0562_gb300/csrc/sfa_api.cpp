@@ -229,17 +229,18 @@ void fill_text_map(TextDesc &d, CUtensorMap &map) {
     }();
     d.rows2d = 0;
     std::memset(&map, 0, sizeof map);
-    const uint64_t rows = d.chunk ? d.n / d.chunk : 0;
+    const uint8_t *base = d.text + d.origin;   // chunk 0's body, then chunk k at base + k*chunk
+    const uint64_t rows = d.chunk && d.n > d.origin ? (d.n - d.origin) / d.chunk : 0;
     if (!encode || d.forced || d.chunk % 16 || d.chunk > 0xffffffffull ||
-        (reinterpret_cast<uintptr_t>(d.text) & 15) || rows == 0 || rows >= (1ull << 31))
+        (reinterpret_cast<uintptr_t>(base) & 15) || rows == 0 || rows >= (1ull << 31))
         return;
-    // the text's full chunks as a [rows][chunk] byte matrix; boxes of
-    // 32 chunks x SLICE bytes, 64-byte swizzled in shared memory
+    // the chunk bodies as a [rows][chunk] byte matrix; boxes of 32 chunks x
+    // SLICE bytes, 64-byte swizzled in shared memory
     const cuuint64_t dims[2] = {d.chunk, rows};
     const cuuint64_t strides[1] = {d.chunk};
     const cuuint32_t box[2] = {(cuuint32_t)sfa_dev::SLICE, 32};
     const cuuint32_t estr[2] = {1, 1};
-    if (encode(&map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<uint8_t *>(d.text), dims, strides, box, estr,
+    if (encode(&map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<uint8_t *>(base), dims, strides, box, estr,
                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS)
         d.rows2d = (uint32_t)rows;
@@ -288,7 +289,9 @@ uint64_t plan_two_levels(const Shape &sh, uint64_t n, TextDesc &d) {
     if (n < 4 * per * 256) return 0;
     const uint64_t la = align_up((n / 1000000 * OLDER_SHARE_PPM + n % 1000000 * OLDER_SHARE_PPM / 1000000 + per - 1) / per,
                                  (uint64_t)sfa_dev::SLICE);
-    const uint64_t split = per * la;
+    // level B starts on a 16-byte boundary: level A is the origin and per
+    // chunks of la bytes
+    const uint64_t split = d.origin + per * la;
     if (split >= n) return 0;
     const uint64_t rest = n - split;
     const uint64_t lb = std::max<uint64_t>(256, align_up((rest + per - 1) / per, (uint64_t)sfa_dev::SLICE));
@@ -330,6 +333,7 @@ int match_impl(sfa_handle *h, const uint8_t *d_text, uint64_t n, sfa_result *d_o
     d.table = 0;
     d.out_index = 0;
     d.carry = carry ? 1u : 0u;
+    d.origin = d.forced ? 0u : sfa_dev::text_origin(d_text);
     const uint64_t cpt = sh.tile_chunks();
     // chunk indices (and, in simulation mode, the ids nr + chunk) stay below 2^31
     if (sfa_dev::num_chunks(d) >= (1ull << 31) - 256) return SFA_ERR_INVALID;
@@ -558,6 +562,7 @@ int plan_into_scratch(sfa_handle_t h, const uint8_t *d_text, uint64_t n, const s
         d.n = n;
         d.chunk = sh.chunk;
         d.forced = 0;
+        d.origin = sfa_dev::text_origin(d_text);
         const uint64_t cpt = sh.tile_chunks();
         if (sfa_dev::num_chunks(d) >= (1ull << 31) - 256) continue;
         uint64_t tiles = plan_two_levels(sh, n, d);

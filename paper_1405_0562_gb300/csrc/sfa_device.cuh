@@ -653,7 +653,9 @@ __global__ void __launch_bounds__(THREADS, (min_ctas_per_sm<THREADS, CH, SIMNQ, 
         const uint64_t lend = d.split_tile != 0 && !lvb ? d.split : d.n;
         const uint64_t lchunk = lvb ? d.chunk_b : d.chunk;
         const uint32_t lrows = lvb ? d.rows2d_b : d.rows2d;
-        uint64_t nch = d.forced ? d.forced : (lend - lbase + lchunk - 1) / lchunk;
+        // level A's origin (level B starts on a 16-byte boundary)
+        const uint64_t org = lvb ? 0 : d.origin;
+        uint64_t nch = d.forced ? d.forced : (lend - lbase > org ? (lend - lbase - org + lchunk - 1) / lchunk : 1);
         if (nch == 0) nch = 1;   // the empty text: one empty chunk
         TextState *ts = S.texts + (BATCH ? ti : 0u);
         const uint8_t *text = d.text;
@@ -683,14 +685,17 @@ __global__ void __launch_bounds__(THREADS, (min_ctas_per_sm<THREADS, CH, SIMNQ, 
                 lo[c] = k * d.n / d.forced;
                 hi[c] = (k + 1) * d.n / d.forced;
             } else {
-                lo[c] = lbase + k * lchunk;
-                hi[c] = lo[c] + lchunk < lend ? lo[c] + lchunk : lend;
+                lo[c] = k == 0 ? lbase : lbase + org + k * lchunk;
+                const uint64_t e = lbase + org + (k + 1) * lchunk;
+                hi[c] = e < lend ? e : lend;
             }
-            // body: the 16-byte-aligned addresses inside [lo, hi)
+            // body: the 16-byte-aligned addresses inside [lo, hi) (empty when
+            // there are none: b wraps around when hi < 16 and the boundary
+            // below text + hi lies before the text)
             const uint64_t a = (((tbase + lo[c]) + 15) & ~(uintptr_t)15) - tbase;
             const uint64_t b = ((tbase + hi[c]) & ~(uintptr_t)15) - tbase;
             ba[c] = a < hi[c] ? a : hi[c];
-            bb[c] = b > ba[c] ? b : ba[c];
+            bb[c] = b > ba[c] && b <= hi[c] ? b : ba[c];
             ch[c].f = T.ident;
             ch[c].cnt = 0;
             ch[c].snap = 0;

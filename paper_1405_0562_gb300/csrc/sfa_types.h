@@ -51,9 +51,14 @@ struct TextDesc {
     uint32_t out_index;
     uint32_t carry;            // 1: continue from out[out_index] (Lemma 1)
     uint32_t rows2d;           // chunks [0, rows2d) are rows of the kernel's
-                               // tensor map (full chunks of an aligned text);
-                               // 0: no tensor map
-    uint32_t pad;
+                               // tensor map (their bodies: full chunks that
+                               // start on a 16-byte boundary); 0: no map
+    // bytes before the text's first 16-byte boundary (0 with forced chunk
+    // counts): level A's chunk 0 is [0, origin + chunk), chunk k >= 1 is
+    // [origin + k*chunk, origin + (k+1)*chunk), so that every chunk body
+    // starts on a 16-byte boundary (Theorem 3: any division of the text
+    // gives the same result)
+    uint32_t origin;
 };
 
 struct TextState {             // zeroed before each launch
@@ -84,10 +89,18 @@ struct Scratch {
     uint32_t total_tiles;
 };
 
+// chunks of a one-level text (the empty text, and one shorter than its
+// origin, have one chunk)
 SFA_HD inline uint64_t num_chunks(const TextDesc &d) {
     if (d.forced) return d.forced;
-    uint64_t c = (d.n + d.chunk - 1) / d.chunk;
+    const uint64_t body = d.n > d.origin ? d.n - d.origin : 0;
+    uint64_t c = (body + d.chunk - 1) / d.chunk;
     return c ? c : 1;
+}
+
+// the origin of a text that starts at p
+SFA_HD inline uint32_t text_origin(const uint8_t *p) {
+    return (uint32_t)((16u - ((uint32_t)(uintptr_t)p & 15u)) & 15u);
 }
 
 // ---------------------------------------------------------------------------

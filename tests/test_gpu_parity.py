@@ -212,6 +212,72 @@ def test_unaligned_text(offset):
         assert sfa_mod().decode(out)[0] == expect(d, base[offset:offset + n])
 
 
+@pytest.mark.parametrize("offset", [1, 3, 8, 15])
+def test_unaligned_text_automatic_chunks(offset):
+    """Texts that start off a 16-byte boundary: the chunks are anchored at
+    the first boundary (chunk 0 takes the bytes before it), so the tensor
+    maps cover them too.  Lengths shorter than, equal to and just past the
+    origin, several tiles with a ragged tail, both tilings, forced chunk
+    counts (no anchoring) and the simulation path."""
+    sfa = sfa_mod()
+    for name in ("ac_set", "r5", "T4"):
+        d = AUTOMATA[name]()
+        a = sfa.Automaton.from_dfa(d)
+        base = text_for(d, (3 << 20) + 64, seed=offset)
+        buf = torch.from_numpy(base).cuda()
+        org = (16 - offset) % 16
+        for n in (0, 1, org - 1, org, org + 1, 4095, 600_001, (3 << 20) + 7):
+            if n < 0:
+                continue
+            want = expect(d, base[offset:offset + n])
+            view = buf[offset:offset + n]
+            for launch in ({}, {"tiling": sfa.TILING_WARP}, {"chunk_bytes": 64}, {"chunk_bytes": 48},
+                           {"forced_chunks": 37}, {"block_threads": 128, "chains": 2, "chunk_bytes": 256}):
+                out = a.match(view, **launch)
+                torch.cuda.synchronize()
+                assert sfa.decode(out)[0] == want, (name, n, launch)
+    d = AUTOMATA["rand8"]()
+    a = sfa.Automaton(d.delta, d.q0, d.accept, mode=sfa.MODE_SIM)
+    base = text_for(d, 700_064, seed=offset)
+    buf = torch.from_numpy(base).cuda()
+    for n in (5, 70_001, 700_000):
+        out = a.match(buf[offset:offset + n])
+        torch.cuda.synchronize()
+        assert sfa.decode(out)[0] == expect(d, base[offset:offset + n]), n
+
+
+def test_batch_of_unaligned_views():
+    """A batch of views at every offset of one buffer (texts shorter than
+    their origin included), alone and in the mix, with its CUDA graph."""
+    sfa = sfa_mod()
+    autos_d = W.workload_batch_automata(3) + [W.dfa_rn(3)]
+    autos = [sfa.Automaton.from_dfa(d) for d in autos_d]
+    rng = np.random.default_rng(7)
+    lens = [int(x) for x in rng.integers(0, 20, 12)] + [int(x) for x in rng.integers(100, 3 << 20, 36)]
+    gaps = rng.integers(0, 16, len(lens))
+    total = int(sum(lens) + gaps.sum()) + 16
+    big = W.text_uniform(total, W.LOWER_ALPHABET, 99)
+    dev = torch.from_numpy(big).cuda()
+    views, hs, want, pos = [], [], [], 1
+    for i, n in enumerate(lens):
+        pos += int(gaps[i])
+        j = i % len(autos)
+        views.append(dev[pos:pos + n])
+        hs.append(autos[j])
+        want.append(expect(autos_d[j], big[pos:pos + n]))
+        pos += n
+    b = sfa.Batch(hs, views)
+    for graph in (False, True, True):
+        out = torch.zeros(16 * len(views), dtype=torch.uint8, device="cuda")
+        b.launch(out, graph=graph)
+        torch.cuda.synchronize()
+        assert sfa.decode(out) == want
+    for i in range(0, len(views), 5):
+        out = hs[i].match(views[i])
+        torch.cuda.synchronize()
+        assert sfa.decode(out)[0] == want[i], i
+
+
 def test_literal_boundaries_inside_chunks():
     """Plants straddling chunk and tile boundaries."""
     lit = b"needle!"

@@ -61,6 +61,14 @@ def test_noalloc_equals_match_twice(sfa):
             assert noalloc(sfa, a, tt, out, stream) == sfa.OK
             stream.synchronize()
             assert sfa.decode(out)[0] == want
+        # the same text from an address off a 16-byte boundary
+        view = tt[5:]
+        ref = a.match(view, stream=stream)
+        out = torch.zeros(16, dtype=torch.uint8, device="cuda")
+        assert noalloc(sfa, a, view, out, stream) == sfa.OK
+        stream.synchronize()
+        f, acc, c = oracle.dfa_run(d.delta, d.q0, d.accept, t[5:])
+        assert sfa.decode(out)[0] == sfa.decode(ref)[0] == (f, acc, 0, c)
         # a shorter text right after a longer one: stale descriptors must not leak
         out = torch.zeros(16, dtype=torch.uint8, device="cuda")
         assert noalloc(sfa, a, tt[:1000], out, stream) == sfa.OK
