@@ -26,11 +26,11 @@ struct sfa_batch {
     size_t smem = 0;
     bool reserved = false;
     uint64_t chunk = 0;                 // chunk length of texts that fill a tile
-    // capacity and device layout: [tables][descriptors][tile map: count, then tile -> text]
+    // capacity and device layout: [tables][descriptors][tensor maps][tile map:
+    // count, then grab position -> tile, then tile -> text]
     int32_t cap_texts = 0;
     uint64_t cap_tiles = 0;
     uint32_t nr_max = 0;
-    // [tables][descriptors][tensor maps][tile map]
     size_t off_tabs = 0, off_descs = 0, off_maps = 0, off_tt = 0, mem_bytes = 0;
     uint8_t *d_mem = nullptr;
     uint8_t *d_scratch = nullptr;
@@ -61,7 +61,7 @@ void set_layout(sfa_batch *b) {
     b->off_descs = align_up((size_t)b->cap_texts * sizeof(Tables), 256);
     b->off_maps = align_up(b->off_descs + (size_t)b->cap_texts * sizeof(TextDesc), 256);
     b->off_tt = align_up(b->off_maps + (size_t)b->cap_texts * sizeof(CUtensorMap), 256);
-    b->mem_bytes = align_up(b->off_tt + (size_t)(1 + b->cap_tiles) * 4, 256);
+    b->mem_bytes = align_up(b->off_tt + (size_t)(1 + 2 * b->cap_tiles) * 4, 256);
 }
 
 // Chunk length of one text: `chunk`, shortened for texts that would not fill
@@ -91,7 +91,12 @@ int check_inputs(const sfa_handle_t *hs, const uint8_t *const *d_texts, const ui
 }
 
 // Builds the work list of the texts into `img` (the device layout of b):
-// texts sorted by automaton (stable), every text's tiles consecutive.
+// texts sorted by automaton (stable), every text's tiles consecutive (tile
+// ids: the look-back walks a text's tiles by id).  CTAs take the tiles in
+// another order: texts by decreasing chunk-length class (a tile lasts about
+// as long as its chunks), automata still grouped within a class, each text's
+// tiles in id order (a tile's look-back only waits for tiles taken before
+// it), so that the last tiles taken are the shortest.
 int fill_worklist(sfa_batch *b, const sfa_handle_t *hs, const uint8_t *const *d_texts, const uint64_t *lens,
                   int32_t k, uint8_t *img) {
     const uint64_t cpt = (uint64_t)b->shape.threads * b->shape.chains;
@@ -124,6 +129,7 @@ int fill_worklist(sfa_batch *b, const sfa_handle_t *hs, const uint8_t *const *d_
     uint32_t *tt = reinterpret_cast<uint32_t *>(img + b->off_tt);
     for (size_t j = 0; j < distinct.size(); ++j) tabs[j] = distinct[j]->dev;
     uint64_t tiles = 0;
+    std::vector<uint32_t> text_of;   // tile id -> text
     for (size_t j = 0; j < order.size(); ++j) {
         const int32_t i = order[j];
         TextDesc d{};
@@ -145,17 +151,25 @@ int fill_worklist(sfa_batch *b, const sfa_handle_t *hs, const uint8_t *const *d_
         fill_text_map(d, map);
         std::memcpy(img + b->off_maps + j * sizeof(CUtensorMap), &map, sizeof map);
         d.map = d.rows2d ? b->d_mem + b->off_maps + j * sizeof(CUtensorMap) : nullptr;
-        for (uint64_t u = 0; u < t; ++u) tt[1 + tiles + u] = (uint32_t)j;
+        text_of.insert(text_of.end(), t, (uint32_t)j);
         tiles += t;
         descs[j] = d;
     }
+    std::vector<uint32_t> by(order.size());
+    for (size_t j = 0; j < by.size(); ++j) by[j] = (uint32_t)j;
+    auto cls = [&](uint32_t j) { return 63 - __builtin_clzll(std::max<uint64_t>(descs[j].chunk, 1)); };
+    std::stable_sort(by.begin(), by.end(), [&](uint32_t x, uint32_t y) { return cls(x) > cls(y); });
     tt[0] = (uint32_t)tiles;
+    uint64_t pos = 0;
+    for (uint32_t j : by)
+        for (uint32_t u = 0; u < descs[j].ntiles; ++u) tt[1 + pos++] = descs[j].tile_base + u;
+    std::memcpy(tt + 1 + tiles, text_of.data(), text_of.size() * sizeof(uint32_t));
     b->k = k;
     b->total_tiles = (uint32_t)tiles;
     b->used_tabs = distinct.size() * sizeof(Tables);
     b->used_descs = order.size() * sizeof(TextDesc);
     b->used_maps = order.size() * sizeof(CUtensorMap);
-    b->used_tt = (size_t)(1 + tiles) * 4;
+    b->used_tt = (size_t)(1 + 2 * tiles) * 4;
     return SFA_OK;
 }
 

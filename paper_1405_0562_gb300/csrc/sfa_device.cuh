@@ -639,7 +639,10 @@ __global__ void __launch_bounds__(THREADS, (min_ctas_per_sm<THREADS, CH, SIMNQ, 
         }
 
         uint32_t ti = 0;
-        if (BATCH) ti = __ldg(tile_text + 1 + gt);
+        if (BATCH) {
+            gt = __ldg(tile_text + 1 + gt);           // grab position -> tile id
+            ti = __ldg(tile_text + 1 + total + gt);   // tile id -> text
+        }
         const TextDesc d = BATCH ? descs[ti] : desc;
         const Tables T = BATCH ? tabs[d.table] : tab;
         const uint32_t tabidx = BATCH ? d.table : 0u;
