@@ -81,6 +81,9 @@ typedef struct {
 
 #define SFA_COMPILE_HOST_ONLY 1u  /* build the tables on the host only; no device
                                      memory, match calls fail with SFA_ERR_HOST_ONLY */
+#define SFA_COMPILE_NO_BANK_TUNE 2u  /* keep the breadth-first numbering of the kept
+                                     states (final states last) instead of choosing the
+                                     ids against shared-memory bank conflicts */
 
 typedef struct {
     uint32_t cap_states;    /* max non-constant D-SFA states; 0 = 65536 */
@@ -102,12 +105,32 @@ typedef struct {
  * over the states reachable from q0 and over byte classes (bytes whose
  * columns of delta are equal); when it has more than cap_states
  * non-constant mappings the handle uses the simulation path (Alg. 3), which
- * is not an error.  Errors: INVALID (range), UNSUPPORTED (nq > 256, or a
- * simulation handle with more than 64 reachable states), OOM, CUDA,
- * NO_DEVICE.
+ * is not an error.  The kept states are numbered breadth first from q0,
+ * final states last; unless SFA_COMPILE_NO_BANK_TUNE is set, the ids within
+ * each kind are then chosen by a local search that lowers the modelled
+ * shared-memory bank conflicts of the kernel's DFA-row lookups (lanes run
+ * over bytes drawn uniformly from the bytes that can change a state; about
+ * 20-40 ms of host time for 50-160 states).  Numbering never changes a result.
+ * Errors: INVALID (range), UNSUPPORTED (nq > 256, or a simulation handle
+ * with more than 64 reachable states), OOM, CUDA, NO_DEVICE.
  */
 int sfa_compile(const int32_t *delta, int32_t nq, int32_t q0, const uint8_t *accept,
                 const sfa_compile_opts *opts, sfa_handle_t *out);
+
+/*
+ * sfa_compile_sample -- sfa_compile with the bank-conflict model of the
+ * state numbering driven by a sample of the texts to come instead of
+ * uniform bytes (the lanes of the model start at pseudo-random offsets of
+ * the sample).  The paper has no counterpart: it only changes where DFA rows
+ * sit in shared memory, never a result.
+ *   sample      host bytes, read during the call only (not kept)
+ *   sample_len  bytes of sample; below 1456 the uniform model is used
+ * Ignored with SFA_COMPILE_NO_BANK_TUNE.  Errors: as sfa_compile, and
+ * INVALID for sample == NULL with sample_len > 0.
+ */
+int sfa_compile_sample(const int32_t *delta, int32_t nq, int32_t q0, const uint8_t *accept,
+                       const sfa_compile_opts *opts, const uint8_t *sample, uint64_t sample_len,
+                       sfa_handle_t *out);
 
 /* sfa_destroy -- frees a handle (NULL is fine).  The caller guarantees that
  * no work using it is in flight. */

@@ -26,7 +26,7 @@ OK, ERR_INVALID, ERR_UNSUPPORTED, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_NO_DEVICE,
 ERR_SCRATCH_LIMIT = -8
 NOALLOC_SCRATCH_BYTES = 4 << 20
 MODE_AUTO, MODE_SFA, MODE_SIM = 0, 1, 2
-COMPILE_HOST_ONLY = 1
+COMPILE_HOST_ONLY, COMPILE_NO_BANK_TUNE = 1, 2
 STATUS_OK, STATUS_TIMEOUT = 0, 1
 DEBUG_SKIP_PUBLISH = 1
 TABLE_CLASS, TABLE_DFA, TABLE_NC, TABLE_MAPS, TABLE_ORIG = 0, 1, 2, 3, 4
@@ -35,7 +35,7 @@ RESULT_BYTES = 16
 
 # every symbol include/sfa.h declares
 EXPORTED = (
-    "sfa_compile", "sfa_destroy", "sfa_info", "sfa_export", "sfa_strerror",
+    "sfa_compile", "sfa_compile_sample", "sfa_destroy", "sfa_info", "sfa_export", "sfa_strerror",
     "sfa_match", "sfa_match_ex", "sfa_match_continue", "sfa_match_host",
     "sfa_batch_create", "sfa_batch_launch", "sfa_batch_graph_launch", "sfa_batch_destroy",
     "sfa_match_batch", "sfa_kernel_launch_count", "sfa_match_noalloc",
@@ -106,6 +106,7 @@ def lib():
     L = ctypes.CDLL(LIB_PATH)
     P, i32, u32, u64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_uint32, ctypes.c_uint64
     L.sfa_compile.argtypes = [P, i32, i32, P, P, ctypes.POINTER(P)]
+    L.sfa_compile_sample.argtypes = [P, i32, i32, P, P, P, u64, ctypes.POINTER(P)]
     L.sfa_destroy.argtypes = [P]
     L.sfa_destroy.restype = None
     L.sfa_info.argtypes = [P, ctypes.POINTER(Info)]
@@ -200,15 +201,24 @@ class Automaton:
     """A DFA compiled into a device-resident D-SFA (or simulation) handle."""
 
     def __init__(self, delta, q0: int, accept, cap_states: int = 0, mode: int = MODE_AUTO,
-                 host_only: bool = False):
+                 host_only: bool = False, bank_tune: bool = True, sample=None):
+        """sample: host bytes (numpy uint8) like the texts to come, for the
+        bank-conflict model of the state numbering (sfa_compile_sample)."""
         d = np.ascontiguousarray(delta, dtype=np.int32)
         a = np.ascontiguousarray(accept, dtype=np.uint8)
         if d.ndim != 2 or d.shape[1] != 256 or a.shape != (d.shape[0],):
             raise ValueError("delta must be int32 [nq, 256] and accept uint8 [nq]")
-        opts = CompileOpts(cap_states, mode, COMPILE_HOST_ONLY if host_only else 0, 0)
+        flags = (COMPILE_HOST_ONLY if host_only else 0) | (0 if bank_tune else COMPILE_NO_BANK_TUNE)
+        opts = CompileOpts(cap_states, mode, flags, 0)
         h = ctypes.c_void_p()
-        _check(lib().sfa_compile(d.ctypes.data, d.shape[0], int(q0), a.ctypes.data, ctypes.byref(opts),
-                                 ctypes.byref(h)), "sfa_compile")
+        if sample is None:
+            _check(lib().sfa_compile(d.ctypes.data, d.shape[0], int(q0), a.ctypes.data, ctypes.byref(opts),
+                                     ctypes.byref(h)), "sfa_compile")
+        else:
+            smp = np.ascontiguousarray(sample, dtype=np.uint8)
+            _check(lib().sfa_compile_sample(d.ctypes.data, d.shape[0], int(q0), a.ctypes.data, ctypes.byref(opts),
+                                            smp.ctypes.data if smp.size else None, smp.size, ctypes.byref(h)),
+                   "sfa_compile_sample")
         self._h = h
         self.nq = d.shape[0]
 

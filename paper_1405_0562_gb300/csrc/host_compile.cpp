@@ -5,7 +5,8 @@
 //  1. validate the DFA (Sect. II-B: total table, one initial state);
 //  2. keep the states reachable from q0 -- every state a chunk can be
 //     entered in is one of them -- and renumber them so that the final
-//     states are the ids [first_accept, nr);
+//     states are the ids [first_accept, nr); within each kind the ids are
+//     then chosen against shared-memory bank conflicts (bank_layout.cpp);
 //  3. merge bytes whose columns of delta are equal into classes (the
 //     alphabet Sigma of Alg. 4 becomes the set of classes);
 //  4. breadth-first correspondence construction from f_I over the classes,
@@ -54,8 +55,12 @@ uint32_t acc_class(const uint8_t *f, int nr, int first_accept) {
 
 }  // namespace
 
-int build_tables(const int32_t *delta, int32_t nq, int32_t q0, const uint8_t *accept,
-                 uint32_t cap, int32_t force_mode, HostTables &T) {
+namespace {
+
+// Steps 1-5 with the kept states numbered breadth first (final states last),
+// then renumbered by `renumber` (new id of every such id) when given.
+int build_numbered(const int32_t *delta, int32_t nq, int32_t q0, const uint8_t *accept, uint32_t cap,
+                   int32_t force_mode, HostTables &T, const std::vector<int32_t> *renumber) {
     auto t0 = std::chrono::steady_clock::now();
     if (!delta || !accept) return SFA_ERR_INVALID;
     if (nq < 1) return SFA_ERR_INVALID;
@@ -88,14 +93,22 @@ int build_tables(const int32_t *delta, int32_t nq, int32_t q0, const uint8_t *ac
     T.first_accept = (int32_t)T.orig_of.size();
     for (int32_t s : order)
         if (accept[s]) T.orig_of.push_back(s);
-    T.kept_of.assign(nq, -1);
-    for (int32_t i = 0; i < T.nr; ++i) T.kept_of[T.orig_of[i]] = i;
-    T.q0 = T.kept_of[q0];
     const int nr = T.nr;
-    T.dfa.assign((size_t)nr * 256, 0);
-    for (int i = 0; i < nr; ++i)
-        for (int b = 0; b < 256; ++b)
-            T.dfa[(size_t)i * 256 + b] = (uint8_t)T.kept_of[delta[(int64_t)T.orig_of[i] * 256 + b]];
+    auto number = [&]() {
+        T.kept_of.assign(nq, -1);
+        for (int32_t i = 0; i < nr; ++i) T.kept_of[T.orig_of[i]] = i;
+        T.q0 = T.kept_of[q0];
+        T.dfa.assign((size_t)nr * 256, 0);
+        for (int i = 0; i < nr; ++i)
+            for (int b = 0; b < 256; ++b)
+                T.dfa[(size_t)i * 256 + b] = (uint8_t)T.kept_of[delta[(int64_t)T.orig_of[i] * 256 + b]];
+    };
+    if (renumber) {
+        std::vector<int32_t> orig(nr);
+        for (int i = 0; i < nr; ++i) orig[(*renumber)[i]] = T.orig_of[i];
+        T.orig_of = orig;
+    }
+    number();
 
     // 3. byte classes: equal columns of the kept table, numbered by first byte
     {
@@ -197,6 +210,24 @@ int build_tables(const int32_t *delta, int32_t nq, int32_t q0, const uint8_t *ac
     }
     T.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     return SFA_OK;
+}
+
+}  // namespace
+
+// The bank-conflict numbering applies to D-SFA handles only: the simulation
+// path looks up |Q| rows per byte and lane, which the model does not describe.
+int build_tables(const int32_t *delta, int32_t nq, int32_t q0, const uint8_t *accept,
+                 uint32_t cap, int32_t force_mode, HostTables &T, bool tune_banks, const uint8_t *sample,
+                 uint64_t sample_len) {
+    auto t0 = std::chrono::steady_clock::now();
+    int rc = build_numbered(delta, nq, q0, accept, cap, force_mode, T, nullptr);
+    if (rc || !tune_banks || T.mode != SFA_MODE_SFA || T.nr < 3) return rc;
+    const std::vector<int32_t> id = bank_numbering(T.dfa, T.nr, T.first_accept, T.q0, sample, sample_len);
+    bool moved = false;
+    for (int32_t i = 0; i < T.nr; ++i) moved |= id[i] != i;
+    if (moved) rc = build_numbered(delta, nq, q0, accept, cap, force_mode, T, &id);
+    T.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    return rc;
 }
 
 }  // namespace sfa_impl

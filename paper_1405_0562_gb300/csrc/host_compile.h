@@ -34,8 +34,17 @@ struct HostTables {
     double seconds = 0.0;
 };
 
-// Returns SFA_OK or an SFA_ERR_* code (see sfa.h for the rules).
+// Returns SFA_OK or an SFA_ERR_* code (see sfa.h for the rules).  tune_banks:
+// number the kept states against shared-memory bank conflicts, modelled on
+// `sample` (host bytes) when it is long enough, else on bytes drawn uniformly
+// from the bytes that can change a state.
 int build_tables(const int32_t *delta, int32_t nq, int32_t q0, const uint8_t *accept,
-                 uint32_t cap, int32_t force_mode, HostTables &out);
+                 uint32_t cap, int32_t force_mode, HostTables &out, bool tune_banks = false,
+                 const uint8_t *sample = nullptr, uint64_t sample_len = 0);
+
+// The search of bank_layout.cpp: new id of every kept id (a permutation that
+// keeps [0, first_accept) and [first_accept, nr) in place as sets).
+std::vector<int32_t> bank_numbering(const std::vector<uint8_t> &dfa, int nr, int first_accept, int q0,
+                                    const uint8_t *sample, uint64_t sample_len);
 
 }  // namespace sfa_impl

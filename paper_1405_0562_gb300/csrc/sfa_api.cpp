@@ -376,15 +376,23 @@ extern "C" {
 
 int sfa_compile(const int32_t *delta, int32_t nq, int32_t q0, const uint8_t *accept,
                 const sfa_compile_opts *opts, sfa_handle_t *out) {
+    return sfa_compile_sample(delta, nq, q0, accept, opts, nullptr, 0, out);
+}
+
+int sfa_compile_sample(const int32_t *delta, int32_t nq, int32_t q0, const uint8_t *accept,
+                       const sfa_compile_opts *opts, const uint8_t *sample, uint64_t sample_len,
+                       sfa_handle_t *out) {
     if (!out) return SFA_ERR_INVALID;
     *out = nullptr;
+    if (!sample && sample_len) return SFA_ERR_INVALID;
     sfa_compile_opts o{};
     if (opts) o = *opts;
     sfa_handle *h = new (std::nothrow) sfa_handle();
     if (!h) return SFA_ERR_OOM;
     int rc;
     try {
-        rc = sfa_impl::build_tables(delta, nq, q0, accept, o.cap_states, o.force_mode, h->host);
+        rc = sfa_impl::build_tables(delta, nq, q0, accept, o.cap_states, o.force_mode, h->host,
+                                    !(o.flags & SFA_COMPILE_NO_BANK_TUNE), sample, sample_len);
     } catch (const std::bad_alloc &) {
         rc = SFA_ERR_OOM;
     }

@@ -278,6 +278,32 @@ def test_batch_of_unaligned_views():
         assert sfa.decode(out)[0] == want[i], i
 
 
+def test_state_numberings_agree():
+    """The breadth-first numbering, the one chosen against bank conflicts by
+    the uniform model and the one chosen on a text sample all give the
+    oracle's results: alone, in a batch, and on a two-level text."""
+    sfa = sfa_mod()
+    d, t = W.workload_large(80 << 20)
+    cases = [(d, t)] + [(x, text_for(x, 3 << 20, seed=i)) for i, x in enumerate(W.workload_batch_automata(4))]
+    cases.append((W.dfa_rn(5), W.text_rn_accepted(2 << 20, 5, 3)))
+    for dd, tt in cases:
+        want = expect(dd, tt)
+        autos = [sfa.Automaton.from_dfa(dd, bank_tune=False), sfa.Automaton.from_dfa(dd),
+                 sfa.Automaton.from_dfa(dd, sample=tt[:1 << 20])]
+        dev = torch.from_numpy(tt).cuda()
+        for a in autos:
+            out = a.match(dev)
+            torch.cuda.synchronize()
+            assert sfa.decode(out)[0] == want
+        views = [dev[:1000], dev[1000:1 << 20], dev[(1 << 20) + 5:]]
+        b = sfa.Batch(autos, views)
+        out = b.launch()
+        torch.cuda.synchronize()
+        got = sfa.decode(out)
+        for v, (lo, hi) in enumerate(((0, 1000), (1000, 1 << 20), ((1 << 20) + 5, tt.size))):
+            assert got[v] == expect(dd, tt[lo:hi]), v
+
+
 def test_literal_boundaries_inside_chunks():
     """Plants straddling chunk and tile boundaries."""
     lit = b"needle!"

@@ -241,3 +241,68 @@ def test_noalloc_refusals_need_no_device():
     # a text that fits passes the host checks and then needs a device (and the
     # handle's device tables)
     assert L.sfa_match_noalloc(big.handle, fake, 1 << 20, fake, None) in (sfa.ERR_NO_DEVICE, sfa.ERR_HOST_ONLY)
+
+
+def _kept_dfa(a):
+    """The handle's kept DFA in the caller's ids: {(orig q, byte): orig q'},
+    and the caller id of every kept id."""
+    orig = a.export(sfa.TABLE_ORIG)
+    dfa = a.export(sfa.TABLE_DFA).reshape(-1, 256)
+    return orig, dfa
+
+
+@pytest.mark.parametrize("make", [lambda: W.workload_large(1 << 12)[0], lambda: W.workload_batch_automata(3)[2],
+                                  lambda: W.dfa_rn(5), lambda: W.dfa_kmp(b"abcaab")])
+def test_bank_numbering_is_a_renumbering(make):
+    """The numbering chosen against bank conflicts (uniform model, or a
+    sample's) is a permutation of the breadth-first one that keeps the final
+    states last, and the kept DFA is the same automaton under it: row
+    orig_of[i] of the caller's table, renumbered, for every kept id i."""
+    d = make()
+    base = host(d, bank_tune=False)
+    acc = np.asarray(d.accept, dtype=bool)
+    rng = np.random.default_rng(4)
+    sample = np.frombuffer(d.alphabet, np.uint8)[rng.integers(0, len(d.alphabet), 1 << 16)]
+    tuned = [host(d), host(d, sample=sample)]
+    o0, D0 = _kept_dfa(base)
+    nfin = int((~acc[o0]).sum())
+    assert not acc[o0[:nfin]].any() and acc[o0[nfin:]].all()
+    for a in tuned:
+        o1, D1 = _kept_dfa(a)
+        assert sorted(o1.tolist()) == sorted(o0.tolist())
+        assert not acc[o1[:nfin]].any() and acc[o1[nfin:]].all()   # final states last
+        kept_of = {int(q): i for i, q in enumerate(o1)}
+        for i, q in enumerate(o1):
+            assert [kept_of[int(x)] for x in d.delta[q]] == D1[i].tolist()
+        # the D-SFA has as many states either way (Alg. 4 is structural)
+        assert a.info()["n_sfa_states"] == base.info()["n_sfa_states"]
+        assert a.info()["n_nonconst"] == base.info()["n_nonconst"]
+
+
+def test_bank_numbering_moves_the_hot_states():
+    """On the 127-state Aho-Corasick automaton the search does renumber, and
+    deterministically (two compiles give the same tables)."""
+    d = W.workload_large(1 << 12)[0]
+    o0, _ = _kept_dfa(host(d, bank_tune=False))
+    o1, D1 = _kept_dfa(host(d))
+    o2, D2 = _kept_dfa(host(d))
+    assert (o1 != o0).any()
+    assert (o1 == o2).all() and (D1 == D2).all()
+
+
+def test_compile_sample_arguments():
+    d = W.dfa_ab_star()
+    delta = np.ascontiguousarray(d.delta, dtype=np.int32)
+    acc = np.ascontiguousarray(d.accept, dtype=np.uint8)
+    opts = sfa.CompileOpts(0, 0, sfa.COMPILE_HOST_ONLY, 0)
+    h = ctypes.c_void_p()
+    L = sfa.lib()
+    assert L.sfa_compile_sample(delta.ctypes.data, d.nq, d.q0, acc.ctypes.data, ctypes.byref(opts), None, 5,
+                                ctypes.byref(h)) == sfa.ERR_INVALID
+    assert L.sfa_compile_sample(delta.ctypes.data, d.nq, d.q0, acc.ctypes.data, ctypes.byref(opts), None, 0,
+                                ctypes.byref(h)) == sfa.OK
+    L.sfa_destroy(h)
+    short = np.zeros(10, np.uint8)   # too short for the model: the uniform one is used
+    assert L.sfa_compile_sample(delta.ctypes.data, d.nq, d.q0, acc.ctypes.data, ctypes.byref(opts),
+                                short.ctypes.data, short.size, ctypes.byref(h)) == sfa.OK
+    L.sfa_destroy(h)
