@@ -20,7 +20,7 @@ constexpr uint64_t WARP_TILE_ROUNDS = 1;           // automatic chunks: warp til
 // Two CTAs per SM: the share of the text (parts per million) given to the
 // level of the CTA that starts first on each SM, which runs faster
 #ifndef SFA_OLDER_SHARE_PPM
-#define SFA_OLDER_SHARE_PPM 519000
+#define SFA_OLDER_SHARE_PPM 525000
 #endif
 constexpr uint64_t OLDER_SHARE_PPM = SFA_OLDER_SHARE_PPM;
 constexpr uint64_t MAX_TEXT = 1ull << 40;
