@@ -10,7 +10,7 @@ namespace sfa_impl {
 // for no q, for every q, or for some q only ("mixed")
 enum AccClass : uint32_t { ACC_NONE = 0, ACC_ALL = 1, ACC_MIXED = 2 };
 
-constexpr uint32_t NC_ID_MASK = 0x3fffffffu;
+constexpr uint32_t NC_ID_MASK = 0x1fffffffu;   // bit 29 is the device's point flag
 constexpr int NC_ACC_SHIFT = 30;
 constexpr uint32_t DEFAULT_CAP = 65536;
 constexpr int SIM_MAX_STATES = 64;

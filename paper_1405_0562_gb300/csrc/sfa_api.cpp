@@ -51,20 +51,70 @@ int blocks_per_sm(const void *k, int threads, size_t smem) {
 }
 
 
+// The device's point-mapping encoding of the non-constant rows (see
+// sfa_types.h): with an absorbing non-final state z (the sink), every entry
+// whose target maps all states but one, s, to z carries s and the image p
+// of s instead of the target's id, and pid[s*nr + p] gives the id back.
+// Returns the sink, or NO_SINK (no such state, simulation mode, or 256 kept
+// states, where a byte-wide "no point" marker would be a state).
+uint32_t point_encoding(const HostTables &H, std::vector<uint32_t> &nc, std::vector<uint32_t> &pid) {
+    nc = H.nc;
+    pid.clear();
+    const int nr = H.nr;
+    if (H.mode != SFA_MODE_SFA || nr < 2 || nr > 255 || H.n_nc == 0) return sfa_dev::NO_SINK;
+    int z = -1;
+    for (int q = 0; q < H.first_accept && z < 0; ++q) {
+        bool absorbing = true;
+        for (int b = 0; b < 256 && absorbing; ++b) absorbing = H.dfa[(size_t)q * 256 + b] == q;
+        if (absorbing) z = q;
+    }
+    if (z < 0) return sfa_dev::NO_SINK;
+    std::vector<int32_t> src(H.n_nc, -1), img(H.n_nc, 0);
+    bool any = false;
+    for (uint64_t i = 0; i < H.n_nc; ++i) {
+        const uint8_t *f = H.maps.data() + i * nr;
+        int live = 0, s = -1;
+        for (int q = 0; q < nr; ++q)
+            if (f[q] != z) {
+                ++live;
+                s = q;
+            }
+        if (live == 1) {
+            src[i] = s;
+            img[i] = f[s];
+            any = true;
+        }
+    }
+    if (!any) return sfa_dev::NO_SINK;
+    pid.assign((size_t)nr * nr, 0);
+    for (uint64_t i = 0; i < H.n_nc; ++i)
+        if (src[i] >= 0) pid[(size_t)src[i] * nr + img[i]] = (uint32_t)(nr + i);
+    for (uint32_t &e : nc) {
+        const uint32_t id = e & sfa_dev::NC_ID_MASK;
+        if (id >= (uint32_t)nr && src[id - nr] >= 0)
+            e = (e & ~sfa_dev::NC_ID_MASK) | sfa_dev::NC_POINT | (uint32_t)src[id - nr] << 8 | (uint32_t)img[id - nr];
+    }
+    return (uint32_t)z;
+}
+
 int upload_tables(sfa_handle *h) {
     const auto &H = h->host;
     const size_t nr = (size_t)H.nr;
+    std::vector<uint32_t> nc, pid;
+    const uint32_t sink = point_encoding(H, nc, pid);
     size_t off_dfa = 0;
     size_t off_cls = align_up(off_dfa + nr * 256, 256);
     size_t off_nc = align_up(off_cls + 256, 256);
-    size_t off_maps = align_up(off_nc + H.nc.size() * 4, 256);
+    size_t off_maps = align_up(off_nc + nc.size() * 4, 256);
     size_t off_orig = align_up(off_maps + H.maps.size(), 256);
     size_t off_kept = align_up(off_orig + nr * 4, 256);
-    size_t total = align_up(off_kept + (size_t)H.nq_in * 4, 256);
+    size_t off_pid = align_up(off_kept + (size_t)H.nq_in * 4, 256);
+    size_t total = align_up(off_pid + pid.size() * 4, 256);
     std::vector<uint8_t> img(total, 0);
     std::memcpy(img.data() + off_dfa, H.dfa.data(), H.dfa.size());
     std::memcpy(img.data() + off_cls, H.cls, 256);
-    if (!H.nc.empty()) std::memcpy(img.data() + off_nc, H.nc.data(), H.nc.size() * 4);
+    if (!nc.empty()) std::memcpy(img.data() + off_nc, nc.data(), nc.size() * 4);
+    if (!pid.empty()) std::memcpy(img.data() + off_pid, pid.data(), pid.size() * 4);
     if (!H.maps.empty()) std::memcpy(img.data() + off_maps, H.maps.data(), H.maps.size());
     std::memcpy(img.data() + off_orig, H.orig_of.data(), nr * 4);
     std::memcpy(img.data() + off_kept, H.kept_of.data(), (size_t)H.nq_in * 4);
@@ -83,6 +133,8 @@ int upload_tables(sfa_handle *h) {
     T.maps = h->d_tables + off_maps;
     T.orig_of = reinterpret_cast<const int32_t *>(h->d_tables + off_orig);
     T.kept_of = reinterpret_cast<const int32_t *>(h->d_tables + off_kept);
+    T.pid = pid.empty() ? nullptr : reinterpret_cast<const uint32_t *>(h->d_tables + off_pid);
+    T.sink = sink;
     T.nr = H.nr;
     T.ncls = H.ncls;
     T.first_accept = H.first_accept;

@@ -181,28 +181,54 @@ struct Chain {
     uint32_t cnt;     // positions whose mapping is final for every kept q
     uint32_t snap;    // cnt at the last mixed position
     int32_t lm;       // offset of the last mixed position, -1 if none
+    uint32_t ps;      // source of the point mapping the chunk went through, or NO_POINT
 };
 
 // offset of (state q, byte b) in the shared-memory DFA rows
 __device__ __forceinline__ uint32_t didx(uint32_t q, uint32_t b) { return q * ROWB + b; }
 
-// one symbol of Alg. 5 in the D-SFA: f <- delta_s[f, sigma]
+// one symbol of Alg. 5 in the D-SFA: f <- delta_s[f, sigma].
+// Point mappings {s -> p, others -> sink}: f = NC_POINT | s << 8 | p, and
+// f . delta^sigma = {s -> delta(p, sigma), others -> sink} is one DFA-row
+// lookup.  Entering one sets the last mixed position to the entering byte,
+// so that pass 2 reruns the DFA up to there; after it cnt counts the final
+// p, which are the final positions for the entering state s alone (for any
+// other entering state the chunk is in the non-final sink).  When p falls
+// into the sink the mapping is the constant sink and s.ps keeps s.
 __device__ __forceinline__ void sfa_step(Chain &s, uint32_t b, int32_t j, const uint8_t *s_dfa,
                                          const uint8_t *s_cls, const uint32_t *nc, uint32_t nr,
-                                         uint32_t ncls, uint32_t first_accept) {
-    if (s.f >= nr) {
+                                         uint32_t ncls, uint32_t first_accept, uint32_t sink) {
+    if (s.f & NC_POINT) {
+        const uint32_t p = s_dfa[didx(s.f & 0xffu, b)];
+        s.cnt += p >= first_accept;
+        if (p == sink) {
+            s.ps = (s.f >> 8) & 0xffu;
+            s.f = p;
+        } else {
+            s.f = (s.f & ~0xffu) | p;
+        }
+    } else if (s.f >= nr) {
         const uint32_t e = __ldg(nc + (size_t)(s.f - nr) * ncls + s_cls[b]);
-        s.f = e & NC_ID_MASK;
         // the class bits, without divergent branches
         const uint32_t a = e >> 30;
-        const bool mixed = a == ACC_MIXED;
+        const bool pt = (e & NC_POINT) != 0u;
+        const bool mark = a == ACC_MIXED || pt;
+        s.f = e & (pt ? (NC_POINT | 0xffffu) : NC_ID_MASK);
         s.cnt += a == ACC_ALL;
-        s.lm = mixed ? j : s.lm;
-        s.snap = mixed ? s.cnt : s.snap;
+        s.lm = mark ? j : s.lm;
+        s.snap = mark ? s.cnt : s.snap;
     } else {
         s.f = s_dfa[didx(s.f, b)];
         s.cnt += s.f >= first_accept;
     }
+}
+
+// The count of a chunk entered in state v, from its pass-1 record: the DFA
+// rerun over [lo, lo + lm] (rerun: its value, or 0 when it is added later),
+// then the positions after lm -- all of them if the chunk never became a
+// point mapping, else only for the entering state ps.
+__device__ __forceinline__ uint32_t chunk_count_after(const Chain &c, uint32_t v) {
+    return c.ps == NO_POINT || v == c.ps ? c.cnt - c.snap : 0u;
 }
 
 // 4 symbols of a constant-state chunk, keeping the largest state seen
@@ -703,6 +729,7 @@ __global__ void __launch_bounds__(THREADS, (min_ctas_per_sm<THREADS, CH, SIMNQ, 
             ch[c].cnt = 0;
             ch[c].snap = 0;
             ch[c].lm = -1;
+            ch[c].ps = NO_POINT;
             if (SIMNQ) {
                 // T = f_I over the kept states; padding entries follow state 0
 #pragma unroll
@@ -727,7 +754,7 @@ __global__ void __launch_bounds__(THREADS, (min_ctas_per_sm<THREADS, CH, SIMNQ, 
             if (SIMNQ)
                 sim_byte<NQ>(V[c], ch[c], b, j, s_dfa, A);
             else
-                sfa_step(ch[c], b, j, s_dfa, s_cls, T.nc, nr, T.ncls, A);
+                sfa_step(ch[c], b, j, s_dfa, s_cls, T.nc, nr, T.ncls, A, T.sink);
         };
         auto constant = [&](int c) -> bool { return SIMNQ ? V[c].mode == SIM_CONST : ch[c].f < nr; };
 
@@ -941,6 +968,11 @@ __global__ void __launch_bounds__(THREADS, (min_ctas_per_sm<THREADS, CH, SIMNQ, 
 #pragma unroll
         for (int c = 0; c < CH; ++c) {
             for (uint64_t p = bb[c] > lo[c] ? bb[c] : lo[c]; p < hi[c]; ++p) step(c, text[p], (int32_t)(p - lo[c]));
+            if (!SIMNQ && (ch[c].f & NC_POINT)) {
+                // a point mapping to the end: its D-SFA id for the scan
+                ch[c].ps = (ch[c].f >> 8) & 0xffu;
+                ch[c].f = __ldg(T.pid + ch[c].ps * nr + (ch[c].f & 0xffu));
+            }
             if (SIMNQ) sim_compact<NQ>(V[c], ch[c]);
             if (SIMNQ && V[c].mode != SIM_CONST) {
                 // keep the vector for the scan: id nr + global chunk index
@@ -1010,7 +1042,8 @@ __global__ void __launch_bounds__(THREADS, (min_ctas_per_sm<THREADS, CH, SIMNQ, 
             for (int i = j + 1; i < lane; ++i) v = apply_map(s_f[warp * 32 + i], v, mtab, nr);
             unsigned long long tsum = ch[0].cnt;
             if (ch[0].lm >= 0)
-                tsum = dfa_count(text, lo[0], lo[0] + (uint64_t)ch[0].lm + 1, v, s_dfa, A) + ch[0].cnt - ch[0].snap;
+                tsum = dfa_count(text, lo[0], lo[0] + (uint64_t)ch[0].lm + 1, v, s_dfa, A) +
+                       chunk_count_after(ch[0], v);
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) tsum += __shfl_down_sync(0xffffffffu, tsum, o);
             if (lane == 0) finish_tile(S, T, d, ts, out, tsum, local, incl);
@@ -1089,7 +1122,8 @@ __global__ void __launch_bounds__(THREADS, (min_ctas_per_sm<THREADS, CH, SIMNQ, 
             // tile) deferred until after that tile
             uint32_t s_in = 0;
             if (lane == 0) {
-                const bool first_const = DEFER && tconst && local > 0 && ch[0].f < nr && total > gridDim.x;
+                const bool first_const =
+                    DEFER && tconst && local > 0 && ch[0].f < nr && ch[0].ps == NO_POINT && total > gridDim.x;
                 if (first_const && ch[0].lm < 0) {
                     s_in = 0;   // unused
                 } else if (first_const && ch[0].lm < 64) {
@@ -1148,7 +1182,7 @@ __global__ void __launch_bounds__(THREADS, (min_ctas_per_sm<THREADS, CH, SIMNQ, 
                 // positions after its last mixed one now
                 const bool deferred = DEFER && c == 0 && tid == 0 && s_misc->dfr_valid;
                 cc = (deferred ? 0u : dfa_count(text, lo[c], lo[c] + (uint64_t)ch[c].lm + 1, v, s_dfa, A)) +
-                     ch[c].cnt - ch[c].snap;
+                     chunk_count_after(ch[c], v);
             }
             tsum += cc;
         }

@@ -13,7 +13,15 @@
 
 namespace sfa_dev {
 
-constexpr uint32_t NC_ID_MASK = 0x3fffffffu;
+// A non-constant row entry: next id | acceptance class << 30.  On the device
+// an entry whose target is a point mapping {s -> p, every other q -> sink}
+// (sink: an absorbing non-final state) carries NC_POINT | s << 8 | p instead
+// of the id: the chunk then follows p through the DFA rows (one shared-memory
+// lookup per byte) until it ends or p falls into the sink.
+constexpr uint32_t NC_ID_MASK = 0x1fffffffu;
+constexpr uint32_t NC_POINT = 1u << 29;
+constexpr uint32_t NO_SINK = 0xffffffffu;
+constexpr uint32_t NO_POINT = 0xffffffffu;   // a chunk's point source: none
 constexpr uint32_t ACC_ALL = 1, ACC_MIXED = 2;
 
 // look-back descriptor: flag in bits 62..63, value (a kept DFA state) below
@@ -27,7 +35,9 @@ struct Tables {
     const uint8_t *maps;       // [n_nc*nr]    mappings of non-constant states
     const int32_t *orig_of;    // [nr]
     const int32_t *kept_of;    // [nq_in]
-    uint32_t nr, ncls, first_accept, q0, ident, nq_in, mode, pad;
+    const uint32_t *pid;       // [nr*nr] id of the point mapping {s -> p} at s*nr + p (sink != NO_SINK)
+    uint32_t nr, ncls, first_accept, q0, ident, nq_in, mode;
+    uint32_t sink;             // the sink of the point mappings, or NO_SINK
 };
 
 struct TextDesc {

@@ -304,6 +304,36 @@ def test_state_numberings_agree():
             assert got[v] == expect(dd, tt[lo:hi]), v
 
 
+@pytest.mark.parametrize("name", ["r3", "r5", "ra2", "even_odd5", "ab_star"])
+def test_point_mappings(name):
+    """Automata with an absorbing non-final state: chunk mappings of one live
+    state (the rest dead) are followed through the DFA rows and counted for
+    their source state only.  Texts from cleanly accepted to random (chunks
+    that die into the sink early, late, or never), every tiling, short
+    chunks, forced chunk counts, and a batch."""
+    sfa = sfa_mod()
+    d = AUTOMATA[name]()
+    a = sfa.Automaton.from_dfa(d)
+    alpha = np.frombuffer(d.alphabet, np.uint8)
+    rng = np.random.default_rng(len(name))
+    texts = []
+    for n, rate in (((1 << 20) + 11, 0), ((1 << 20) + 3, 1 / 5000), (600_001, 1 / 300), (300_007, 1 / 20),
+                    (200_003, 1.0)):
+        t = text_for(d, n, seed=n)
+        flips = rng.random(n) < rate
+        t[flips] = alpha[rng.integers(0, alpha.size, int(flips.sum()))]
+        texts.append(t)
+    for t in texts:
+        want = expect(d, t)
+        for launch in ({}, {"tiling": sfa.TILING_WARP}, {"tiling": sfa.TILING_CTA, "chunk_bytes": 100},
+                       {"chunk_bytes": 16, "block_threads": 128, "chains": 2}, {"forced_chunks": 64}):
+            assert gpu_match(a, t, **launch) == want, (name, t.size, launch)
+    dev = [torch.from_numpy(t).cuda() for t in texts]
+    out = sfa.Batch([a] * len(dev), dev).launch()
+    torch.cuda.synchronize()
+    assert sfa.decode(out) == [expect(d, t) for t in texts]
+
+
 def test_literal_boundaries_inside_chunks():
     """Plants straddling chunk and tile boundaries."""
     lit = b"needle!"
