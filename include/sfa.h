@@ -52,7 +52,7 @@ typedef struct sfa_batch *sfa_batch_t;
 /* ---- error codes ------------------------------------------------------- */
 #define SFA_OK               0
 #define SFA_ERR_INVALID     -1  /* bad argument: DFA out of range, NULL pointer, size */
-#define SFA_ERR_UNSUPPORTED -2  /* valid but outside this build's limits (e.g. nq > 256) */
+#define SFA_ERR_UNSUPPORTED -2  /* valid but outside the library's limits (e.g. nq > 256) */
 #define SFA_ERR_OOM         -3  /* host or device allocation failed */
 #define SFA_ERR_CUDA        -4  /* a CUDA runtime call failed */
 #define SFA_ERR_TIMEOUT     -5  /* a device-side bounded wait gave up (see sfa_result.status) */

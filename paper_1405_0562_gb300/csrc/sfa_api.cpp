@@ -517,7 +517,7 @@ const char *sfa_strerror(int code) {
     switch (code) {
         case SFA_OK: return "success";
         case SFA_ERR_INVALID: return "invalid argument";
-        case SFA_ERR_UNSUPPORTED: return "outside the limits of this build";
+        case SFA_ERR_UNSUPPORTED: return "outside the limits of the library";
         case SFA_ERR_OOM: return "out of memory";
         case SFA_ERR_CUDA: return "CUDA runtime error";
         case SFA_ERR_TIMEOUT: return "a device-side bounded wait gave up";

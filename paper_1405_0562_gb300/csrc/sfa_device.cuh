@@ -951,6 +951,23 @@ __global__ void __launch_bounds__(THREADS, (min_ctas_per_sm<THREADS, CH, SIMNQ, 
                             dfa_word(q, cn, v.w, s_dfa, A);
                             ch[c].f = q;
                             ch[c].cnt = cn;
+                        } else if (!SIMNQ && (ch[c].f & NC_POINT)) {
+                            // a point mapping: its live state p through the
+                            // DFA rows, 16 bytes at a time (once p is in the
+                            // absorbing, non-final sink it stays there and
+                            // counts nothing, so the sink is tested once)
+                            uint32_t q = ch[c].f & 0xffu, cn = ch[c].cnt;
+                            dfa_word(q, cn, v.x, s_dfa, A);
+                            dfa_word(q, cn, v.y, s_dfa, A);
+                            dfa_word(q, cn, v.z, s_dfa, A);
+                            dfa_word(q, cn, v.w, s_dfa, A);
+                            ch[c].cnt = cn;
+                            if (q == T.sink) {
+                                ch[c].ps = (ch[c].f >> 8) & 0xffu;
+                                ch[c].f = q;
+                            } else {
+                                ch[c].f = (ch[c].f & ~0xffu) | q;
+                            }
                         } else {
                             const uint32_t ws[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
