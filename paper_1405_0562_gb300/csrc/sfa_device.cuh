@@ -181,7 +181,6 @@ struct Chain {
     uint32_t cnt;     // positions whose mapping is final for every kept q
     uint32_t snap;    // cnt at the last mixed position
     int32_t lm;       // offset of the last mixed position, -1 if none
-    uint32_t ps;      // source of the point mapping the chunk went through, or NO_POINT
 };
 
 // offset of (state q, byte b) in the shared-memory DFA rows
@@ -193,20 +192,16 @@ __device__ __forceinline__ uint32_t didx(uint32_t q, uint32_t b) { return q * RO
 // lookup.  Entering one sets the last mixed position to the entering byte,
 // so that pass 2 reruns the DFA up to there; after it cnt counts the final
 // p, which are the final positions for the entering state s alone (for any
-// other entering state the chunk is in the non-final sink).  When p falls
-// into the sink the mapping is the constant sink and s.ps keeps s.
+// other entering state the chunk is in the non-final sink).  A chunk stays a
+// point mapping to its end, also once p is the sink (then {s -> sink} is
+// the constant sink).
 __device__ __forceinline__ void sfa_step(Chain &s, uint32_t b, int32_t j, const uint8_t *s_dfa,
                                          const uint8_t *s_cls, const uint32_t *nc, uint32_t nr,
-                                         uint32_t ncls, uint32_t first_accept, uint32_t sink) {
+                                         uint32_t ncls, uint32_t first_accept) {
     if (s.f & NC_POINT) {
         const uint32_t p = s_dfa[didx(s.f & 0xffu, b)];
         s.cnt += p >= first_accept;
-        if (p == sink) {
-            s.ps = (s.f >> 8) & 0xffu;
-            s.f = p;
-        } else {
-            s.f = (s.f & ~0xffu) | p;
-        }
+        s.f = (s.f & ~0xffu) | p;
     } else if (s.f >= nr) {
         const uint32_t e = __ldg(nc + (size_t)(s.f - nr) * ncls + s_cls[b]);
         // the class bits, without divergent branches
@@ -227,8 +222,8 @@ __device__ __forceinline__ void sfa_step(Chain &s, uint32_t b, int32_t j, const 
 // rerun over [lo, lo + lm] (rerun: its value, or 0 when it is added later),
 // then the positions after lm -- all of them if the chunk never became a
 // point mapping, else only for the entering state ps.
-__device__ __forceinline__ uint32_t chunk_count_after(const Chain &c, uint32_t v) {
-    return c.ps == NO_POINT || v == c.ps ? c.cnt - c.snap : 0u;
+__device__ __forceinline__ uint32_t chunk_count_after(const Chain &c, uint32_t v, uint32_t ps) {
+    return ps == NO_POINT || v == ps ? c.cnt - c.snap : 0u;
 }
 
 // 4 symbols of a constant-state chunk, keeping the largest state seen
@@ -592,6 +587,11 @@ __global__ void __launch_bounds__(THREADS, (min_ctas_per_sm<THREADS, CH, SIMNQ, 
     const uint32_t bar0 = smem_addr(smem + L::bar_off(nr_max)) + (uint32_t)warp * STAGES * 8;
     uint8_t *s_box = smem + L::stage_off(nr_max) + (size_t)warp * STAGES * CH * BOX;
     uint8_t *s_extra = smem + L::extra_off(nr_max) + (size_t)warp * STAGES * CH * SLICE;
+    // the point source of this lane's chunk of round c (after pass 1)
+    auto point_src = [&](int c) -> uint32_t {
+        const uint8_t v = s_extra[c * 32 + lane];
+        return v == (uint8_t)NO_POINT ? NO_POINT : (uint32_t)v;
+    };
     if (lane == 0)
         for (int s = 0; s < STAGES; ++s) mbar_init(bar0 + 8 * s, 1);
     mbar_init_fence();
@@ -729,7 +729,6 @@ __global__ void __launch_bounds__(THREADS, (min_ctas_per_sm<THREADS, CH, SIMNQ, 
             ch[c].cnt = 0;
             ch[c].snap = 0;
             ch[c].lm = -1;
-            ch[c].ps = NO_POINT;
             if (SIMNQ) {
                 // T = f_I over the kept states; padding entries follow state 0
 #pragma unroll
@@ -754,7 +753,7 @@ __global__ void __launch_bounds__(THREADS, (min_ctas_per_sm<THREADS, CH, SIMNQ, 
             if (SIMNQ)
                 sim_byte<NQ>(V[c], ch[c], b, j, s_dfa, A);
             else
-                sfa_step(ch[c], b, j, s_dfa, s_cls, T.nc, nr, T.ncls, A, T.sink);
+                sfa_step(ch[c], b, j, s_dfa, s_cls, T.nc, nr, T.ncls, A);
         };
         auto constant = [&](int c) -> bool { return SIMNQ ? V[c].mode == SIM_CONST : ch[c].f < nr; };
 
@@ -953,21 +952,14 @@ __global__ void __launch_bounds__(THREADS, (min_ctas_per_sm<THREADS, CH, SIMNQ, 
                             ch[c].cnt = cn;
                         } else if (!SIMNQ && (ch[c].f & NC_POINT)) {
                             // a point mapping: its live state p through the
-                            // DFA rows, 16 bytes at a time (once p is in the
-                            // absorbing, non-final sink it stays there and
-                            // counts nothing, so the sink is tested once)
+                            // DFA rows, 16 bytes at a time
                             uint32_t q = ch[c].f & 0xffu, cn = ch[c].cnt;
                             dfa_word(q, cn, v.x, s_dfa, A);
                             dfa_word(q, cn, v.y, s_dfa, A);
                             dfa_word(q, cn, v.z, s_dfa, A);
                             dfa_word(q, cn, v.w, s_dfa, A);
                             ch[c].cnt = cn;
-                            if (q == T.sink) {
-                                ch[c].ps = (ch[c].f >> 8) & 0xffu;
-                                ch[c].f = q;
-                            } else {
-                                ch[c].f = (ch[c].f & ~0xffu) | q;
-                            }
+                            ch[c].f = (ch[c].f & ~0xffu) | q;
                         } else {
                             const uint32_t ws[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
@@ -985,11 +977,16 @@ __global__ void __launch_bounds__(THREADS, (min_ctas_per_sm<THREADS, CH, SIMNQ, 
 #pragma unroll
         for (int c = 0; c < CH; ++c) {
             for (uint64_t p = bb[c] > lo[c] ? bb[c] : lo[c]; p < hi[c]; ++p) step(c, text[p], (int32_t)(p - lo[c]));
+            // a point mapping to the end: its source s kept for pass 2 in
+            // the warp's extra rows (idle until the next tile's copies), and
+            // its D-SFA id (the constant sink once p is there) for the scan
+            uint32_t ps = NO_POINT;
             if (!SIMNQ && (ch[c].f & NC_POINT)) {
-                // a point mapping to the end: its D-SFA id for the scan
-                ch[c].ps = (ch[c].f >> 8) & 0xffu;
-                ch[c].f = __ldg(T.pid + ch[c].ps * nr + (ch[c].f & 0xffu));
+                ps = (ch[c].f >> 8) & 0xffu;
+                const uint32_t p = ch[c].f & 0xffu;
+                ch[c].f = p == T.sink ? p : __ldg(T.pid + ps * nr + p);
             }
+            s_extra[c * 32 + lane] = (uint8_t)ps;
             if (SIMNQ) sim_compact<NQ>(V[c], ch[c]);
             if (SIMNQ && V[c].mode != SIM_CONST) {
                 // keep the vector for the scan: id nr + global chunk index
@@ -1060,7 +1057,7 @@ __global__ void __launch_bounds__(THREADS, (min_ctas_per_sm<THREADS, CH, SIMNQ, 
             unsigned long long tsum = ch[0].cnt;
             if (ch[0].lm >= 0)
                 tsum = dfa_count(text, lo[0], lo[0] + (uint64_t)ch[0].lm + 1, v, s_dfa, A) +
-                       chunk_count_after(ch[0], v);
+                       chunk_count_after(ch[0], v, point_src(0));
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) tsum += __shfl_down_sync(0xffffffffu, tsum, o);
             if (lane == 0) finish_tile(S, T, d, ts, out, tsum, local, incl);
@@ -1140,7 +1137,7 @@ __global__ void __launch_bounds__(THREADS, (min_ctas_per_sm<THREADS, CH, SIMNQ, 
             uint32_t s_in = 0;
             if (lane == 0) {
                 const bool first_const =
-                    DEFER && tconst && local > 0 && ch[0].f < nr && ch[0].ps == NO_POINT && total > gridDim.x;
+                    DEFER && tconst && local > 0 && ch[0].f < nr && point_src(0) == NO_POINT && total > gridDim.x;
                 if (first_const && ch[0].lm < 0) {
                     s_in = 0;   // unused
                 } else if (first_const && ch[0].lm < 64) {
@@ -1199,7 +1196,7 @@ __global__ void __launch_bounds__(THREADS, (min_ctas_per_sm<THREADS, CH, SIMNQ, 
                 // positions after its last mixed one now
                 const bool deferred = DEFER && c == 0 && tid == 0 && s_misc->dfr_valid;
                 cc = (deferred ? 0u : dfa_count(text, lo[c], lo[c] + (uint64_t)ch[c].lm + 1, v, s_dfa, A)) +
-                     chunk_count_after(ch[c], v);
+                     chunk_count_after(ch[c], v, point_src(c));
             }
             tsum += cc;
         }

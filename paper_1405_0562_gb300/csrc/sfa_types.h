@@ -21,7 +21,7 @@ namespace sfa_dev {
 constexpr uint32_t NC_ID_MASK = 0x1fffffffu;
 constexpr uint32_t NC_POINT = 1u << 29;
 constexpr uint32_t NO_SINK = 0xffffffffu;
-constexpr uint32_t NO_POINT = 0xffffffffu;   // a chunk's point source: none
+constexpr uint32_t NO_POINT = 0xffffffffu;   // a chunk's point source: none (0xff when kept as a byte)
 constexpr uint32_t ACC_ALL = 1, ACC_MIXED = 2;
 
 // look-back descriptor: flag in bits 62..63, value (a kept DFA state) below
