@@ -939,6 +939,22 @@ __global__ void __launch_bounds__(THREADS, (min_ctas_per_sm<THREADS, CH, SIMNQ, 
             } else {
 #pragma unroll
                 for (int c = 0; c < CH; ++c) {
+                    if (!SIMNQ && (ch[c].f & NC_POINT) && len[c] == (uint32_t)SLICE) {
+                        // a point mapping over a full slice: its live state
+                        // through the DFA rows, the slice's 64 bytes unrolled
+                        uint32_t q = ch[c].f & 0xffu, cn = ch[c].cnt;
+#pragma unroll
+                        for (int g = 0; g < SLICE / 16; ++g) {
+                            const uint4 v = *unit(st, c, g);
+                            dfa_word(q, cn, v.x, s_dfa, A);
+                            dfa_word(q, cn, v.y, s_dfa, A);
+                            dfa_word(q, cn, v.z, s_dfa, A);
+                            dfa_word(q, cn, v.w, s_dfa, A);
+                        }
+                        ch[c].cnt = cn;
+                        ch[c].f = (ch[c].f & ~0xffu) | q;
+                        continue;
+                    }
                     const int32_t j0 = (int32_t)(ba[c] + (uint64_t)s * SLICE - lo[c]);
                     for (uint32_t g = 0; 16 * g < len[c]; ++g) {
                         const uint4 v = *unit(st, c, g);
