@@ -133,8 +133,9 @@ constexpr uint32_t ROWB = 264;
 // swizzled, so that 16-byte reads of 8 consecutive lanes hit distinct banks.
 // Chunks that are not a full row (the text's ragged last chunk) take a 1-D
 // bulk copy into the EXTRA row of the warp instead; without a tensor map
-// (unaligned text, forced chunk counts, batches) every lane copies its own
-// slice into its row of the box, unswizzled.
+// (forced chunk counts, chunk lengths that are not multiples of 16) every
+// lane copies its own slice into its row of the box, unswizzled.  After
+// pass 1 the EXTRA rows hold each chunk's point source for pass 2.
 constexpr int SLICE = 64;
 constexpr int STAGES = 2;
 constexpr int BOX = 32 * SLICE;
