@@ -305,7 +305,13 @@ def run_gpu(args, rank: int, world: int, local: int):
     torch.cuda.synchronize()
     barrier(world)
     launches = sfa.kernel_launch_count() - n_before
+    # sustained: the same match back to back for about SUSTAIN_S seconds,
+    # with the clock sampler still running, so that the clock record covers
+    # a window of the same work (the timed region above lasts milliseconds)
+    sustained = sustained_run(torch, stream, lambda: a.match(text, out, stream=stream, **launch), t.size,
+                              step_hint_s=max(1e-5, 1e-3 * t_start.elapsed_time(t_end) / max(1, args.steps)))
     clk = clocks.stop()
+    sustained["sm_mhz_median"] = clk["sm_mhz"]
     total_ms = t_start.elapsed_time(t_end)
     kern_ms = [s.elapsed_time(e) for s, e in evs]
     total_ms = barrier_max(total_ms, world)
@@ -330,16 +336,29 @@ def run_gpu(args, rank: int, world: int, local: int):
     kern_avg = statistics.mean(kern_ms)
     achieved = t.size / (kern_avg * 1e-3) / 1e9
     traffic = profiled_traffic(args.workload)
+    # the same text with the state ids a caller without a sample gets (the
+    # uniform bank-conflict model)
+    a_uni = sfa.Automaton.from_dfa(d)
+    out_u = sfa.empty_results(1, text.device)
+    for _ in range(args.warmup):
+        a_uni.match(text, out_u, stream=stream, **launch)
+    uni_ms = _events(torch, stream, lambda: a_uni.match(text, out_u, stream=stream, **launch), args.steps) / args.steps
+    assert sfa.decode(out_u)[0] == got
+    read_peak = read_only_peak(torch, text.device)
     line = {"metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u8", "data": "synthetic", "config": cfg,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "peak_kind": peak_kind, "kernel": "sfa_match_kernel",
-                         "algorithmic_bytes_per_launch": int(t.size)},
+                         "algorithmic_bytes_per_launch": int(t.size),
+                         "read_only_peak": read_peak, "frac_of_read_only_peak": achieved / read_peak["value"]},
             "e2e": {"value": t.size * world / e2e_s / 1e9, "unit": "GB/s", "h2d_bytes_per_step": int(t.size),
                     "d2h_bytes_per_step": 16},
-            "gpu_launches": int(launches), "clocks": clk}
+            "gpu_launches": int(launches), "clocks": clk, "sustained": sustained,
+            "uniform_numbering": {"value": t.size / (uni_ms * 1e-3) / 1e9, "unit": "GB/s",
+                                  "frac": t.size / (uni_ms * 1e-3) / 1e9 / peak,
+                                  "note": "state ids from the uniform bank-conflict model (no text sample)"}}
     if rank == 0 and not args.no_cpu_baseline:
         base, res = cpu_baseline(d, t)
         line["cpu_baseline"] = base
@@ -348,8 +367,121 @@ def run_gpu(args, rank: int, world: int, local: int):
             a.match(text[:CPU_PARALLEL_SAMPLE], out, stream=stream, **launch)
         stream.synchronize()
         line["cpu_parallel"] = cpu_parallel(d, t, sfa.decode(out)[0][0])
+    if args.workload == "plain_large" and not args.no_side_legs:
+        # short legs of the other configurations, each checked against the
+        # oracle, so that one default run covers them too
+        del text
+        torch.cuda.empty_cache()
+        line["side_legs"] = {"batched_subset": side_batched(torch, sfa, stream, args, rank),
+                             "sim_1GiB": side_sim(torch, sfa, stream, args, rank)}
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+SUSTAIN_S = 2.0
+
+
+def sustained_run(torch, stream, fn, nbytes, step_hint_s):
+    """fn back to back on `stream` for about SUSTAIN_S seconds (CUDA events)."""
+    reps = max(10, int(SUSTAIN_S / step_hint_s))
+    ms = _events(torch, stream, fn, reps)
+    return {"value": nbytes * reps / (ms * 1e-3) / 1e9, "unit": "GB/s", "seconds": ms * 1e-3, "matches": reps}
+
+
+def read_only_peak(torch, device, nbytes=4 << 30, reps=5):
+    """Read-only HBM bandwidth of this GPU, measured here: torch's int64 sum
+    over a buffer of nbytes (larger than L2), best of `reps`."""
+    buf = torch.ones(nbytes // 8, dtype=torch.int64, device=device)
+    buf.sum()
+    torch.cuda.synchronize()
+    best = None
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        buf.sum()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        best = ms if best is None else min(best, ms)
+    del buf
+    torch.cuda.empty_cache()
+    return {"value": nbytes / (best * 1e-3) / 1e9, "unit": "GB/s",
+            "how": f"torch int64 sum over {nbytes >> 30} GiB, best of {reps}"}
+
+
+BATCH_SUBSET = 1024
+
+
+def side_batched(torch, sfa, stream, args, rank):
+    """The first BATCH_SUBSET texts of the batched workload (config 3's
+    lengths, automata and pairing) in one persistent launch under a CUDA
+    graph, against the same texts as plain launches; every result checked
+    against the oracle."""
+    import oracle
+    autos_d = W.workload_batch_automata()
+    autos = [sfa.Automaton.from_dfa(d) for d in autos_d]
+    lens = W.workload_batch_lengths()[:BATCH_SUBSET]
+    pair = W.workload_batch_pairing(len(lens), len(autos))
+    total = int(lens.sum())
+    big = W.text_uniform(total, W.LOWER_ALPHABET, W.SEED_BATCH + 2)
+    offs = np.concatenate([[0], np.cumsum(lens)])
+    dev = torch.from_numpy(big).cuda()
+    views = [dev[offs[i]:offs[i + 1]] for i in range(len(lens))]
+    hs = [autos[p] for p in pair]
+    b = sfa.Batch(hs, views)
+    out = sfa.empty_results(len(views))
+    for _ in range(args.warmup):
+        b.launch(out, stream=stream, graph=True)
+    stream.synchronize()
+    ms = _events(torch, stream, lambda: b.launch(out, stream=stream, graph=True), args.steps) / args.steps
+    got = sfa.decode(out)
+    outs = sfa.empty_results(len(views))
+    plain = lambda: [hs[i].match(views[i], outs[16 * i:16 * i + 16], stream=stream) for i in range(len(views))]
+    plain()
+    pms = _events(torch, stream, plain, 3) / 3
+    exact = sfa.decode(outs) == got
+    if rank == 0:
+        from concurrent.futures import ThreadPoolExecutor
+
+        def ref(i):
+            d = autos_d[pair[i]]
+            f, a, c = oracle.dfa_run(d.delta, d.q0, d.accept, big[offs[i]:offs[i + 1]])
+            return (f, a, 0, c)
+        with ThreadPoolExecutor(os.cpu_count() or 4) as ex:
+            exact = exact and list(ex.map(ref, range(len(views)))) == got
+    del dev, views, b
+    torch.cuda.empty_cache()
+    return {"value": total / (ms * 1e-3) / 1e9, "unit": "GB/s", "texts": len(lens), "text_bytes": total,
+            "ms_per_step": ms, "plain_launches_GBps": total / (pms * 1e-3) / 1e9, "speedup_vs_plain": pms / ms,
+            "bit_exact_vs_oracle": bool(exact),
+            "workload": f"first {len(lens)} texts of the batched workload (log-uniform 256 B..16 MiB, a-z, "
+                        "8 literal-set automata), one graph launch per step"}
+
+
+def side_sim(torch, sfa, stream, args, rank, n=1 << 30):
+    """Simulation mode (random complete DFAs of 16 and 64 states over 16
+    symbols) on 1 GiB; each result checked against the oracle."""
+    import oracle
+    autos_d = [d for d in W.workload_sim_automata() if d.nq in (16, 64)]
+    t = W.workload_sim_text(n)
+    tt = torch.from_numpy(t).cuda()
+    res = {}
+    for d in autos_d:
+        a = sfa.Automaton.from_dfa(d)
+        out = sfa.empty_results(1)
+        for _ in range(args.warmup):
+            a.match(tt, out, stream=stream)
+        ms = _events(torch, stream, lambda: a.match(tt, out, stream=stream), args.steps) / args.steps
+        got = sfa.decode(out)[0]
+        exact = None
+        if rank == 0:
+            f, acc, c = oracle.dfa_run(d.delta, d.q0, d.accept, t)
+            exact = got == (f, acc, 0, c)
+        res[f"{d.nq}_states"] = {"value": n / (ms * 1e-3) / 1e9, "unit": "GB/s", "mode": a.info()["mode"],
+                                 "bit_exact_vs_oracle": exact}
+    del tt
+    torch.cuda.empty_cache()
+    return res
 
 
 def _events(torch, stream, fn, steps):
@@ -696,6 +828,7 @@ def main():
     ap.add_argument("--requests", type=int, default=20000, help="serving: requests per offered load")
     ap.add_argument("--check", action="store_true", help="sim: compare the full outputs with the oracle")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-side-legs", action="store_true", help="plain_large: skip the batched and sim legs")
     ap.add_argument("--text-bytes", type=int, default=0, help="override the text size (profiling runs only)")
     ap.add_argument("--chunk-bytes", type=int, default=0, help="launch shape override (default: automatic)")
     ap.add_argument("--block-threads", type=int, default=0, help="launch shape override (default: automatic)")

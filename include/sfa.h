@@ -111,8 +111,9 @@ typedef struct {
  * shared-memory bank conflicts of the kernel's DFA-row lookups (lanes run
  * over bytes drawn uniformly from the bytes that can change a state; about
  * 20-40 ms of host time for 50-160 states).  Numbering never changes a result.
- * Errors: INVALID (range), UNSUPPORTED (nq > 256, or a simulation handle
- * with more than 64 reachable states), OOM, CUDA, NO_DEVICE.
+ * Errors: INVALID (range), UNSUPPORTED (nq > 256, or SFA_MODE_SFA forced
+ * past the cap), OOM, CUDA, NO_DEVICE.  Every DFA of 1..256 states compiles
+ * in SFA_MODE_AUTO (simulation vectors cover up to 256 reachable states).
  */
 int sfa_compile(const int32_t *delta, int32_t nq, int32_t q0, const uint8_t *accept,
                 const sfa_compile_opts *opts, sfa_handle_t *out);
@@ -260,12 +261,15 @@ int sfa_match_host(sfa_handle_t h, const uint8_t *h_text, uint64_t n, sfa_result
  * SFA_NOALLOC_SCRATCH_BYTES array compiled into the library instead of in
  * handle-owned memory; every GPU that loads the library holds one copy until
  * the process exits.  The caller still passes the text and the result buffer.
- *   - No cudaMalloc, cudaFree or other allocating call is made.  The first
- *     call on a device looks up the array's device address (once per device,
- *     with that device current); make that first call before any stream
- *     capture.
- *   - The handle must be in SFA mode (simulation handles: SFA_ERR_UNSUPPORTED)
- *     and live on the current device (else SFA_ERR_INVALID).
+ *   - No cudaMalloc, cudaFree or other allocating call is made.  Every call
+ *     looks up the array's device address on the current device
+ *     (cudaGetSymbolAddress, which allocates nothing), so no address taken
+ *     before a cudaDeviceReset is used after it; the first call on a device may load the
+ *     library's device code there, so make it before any stream capture.
+ *   - The handle must be in SFA mode (simulation handles: SFA_ERR_UNSUPPORTED),
+ *     have device tables (else SFA_ERR_HOST_ONLY) and live on the current
+ *     device (else SFA_ERR_INVALID).  Every refusal is returned before any
+ *     work is enqueued and before the array's address is looked up.
  *   - A text whose scratch would not fit is rejected with
  *     SFA_ERR_SCRATCH_LIMIT before any work is enqueued.  The scratch is about
  *     8 + nr bytes per tile (nr = reachable states), and the automatic chunk

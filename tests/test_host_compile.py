@@ -164,6 +164,21 @@ def test_random_dfas_exceed_default_cap():
         assert info["mode"] == sfa.MODE_SIM, d.name
 
 
+@pytest.mark.parametrize("nq", [65, 100, 128, 129, 200, 256])
+def test_simulation_up_to_256_states(nq):
+    """Alg. 3 serves every DFA of up to 256 states: random complete DFAs past
+    the D-SFA cap compile in simulation mode (the cycle automaton, whose
+    D-SFA is the nq rotations, stays a D-SFA unless forced)."""
+    info = host(W.dfa_random(nq, 16, seed=nq)).info()
+    assert info["mode"] == sfa.MODE_SIM and info["n_reachable"] <= nq
+    cyc = np.tile((np.arange(nq, dtype=np.int32)[:, None] + 1) % nq, (1, 256))
+    acc = (np.arange(nq) % 3 == 0).astype(np.uint8)
+    a = sfa.Automaton(cyc, 0, acc, host_only=True)
+    assert a.info()["mode"] == sfa.MODE_SFA and a.info()["n_sfa_states"] == nq
+    a = sfa.Automaton(cyc, 0, acc, host_only=True, mode=sfa.MODE_SIM)
+    assert a.info()["mode"] == sfa.MODE_SIM and a.info()["n_reachable"] == nq
+
+
 def test_unreachable_states_are_trimmed():
     d = W.dfa_ab_star()
     delta = np.concatenate([d.delta, np.full((2, 256), 3, dtype=np.int32)])   # states 3, 4 unreachable
@@ -175,7 +190,7 @@ def test_unreachable_states_are_trimmed():
 
 @pytest.mark.parametrize("case,code", [
     ("nq0", sfa.ERR_INVALID), ("nq257", sfa.ERR_UNSUPPORTED), ("range", sfa.ERR_INVALID),
-    ("q0", sfa.ERR_INVALID), ("sim_too_big", sfa.ERR_UNSUPPORTED),
+    ("q0", sfa.ERR_INVALID),
 ])
 def test_invalid_dfas(case, code):
     L = sfa.lib()
@@ -192,10 +207,6 @@ def test_invalid_dfas(case, code):
         delta[2, 7] = 4
     elif case == "q0":
         q0 = 4
-    elif case == "sim_too_big":
-        nq = 80
-        delta = np.tile((np.arange(80, dtype=np.int32)[:, None] + 1) % 80, (1, 256))
-        opts.force_mode = sfa.MODE_SIM
     acc = np.zeros(max(nq, 1), dtype=np.uint8)
     rc = L.sfa_compile(delta.ctypes.data, nq, q0, acc.ctypes.data, ctypes.byref(opts), ctypes.byref(h))
     assert rc == code
@@ -223,24 +234,24 @@ def test_class_compression_is_exact():
 
 
 def test_noalloc_refusals_need_no_device():
-    """sfa_match_noalloc decides every refusal on the host, before it touches
-    a device: checked here with host-only handles (no GPU in this process)."""
+    """sfa_match_noalloc decides every refusal before it enqueues work or looks
+    up its array: checked here with host-only handles (no GPU in this
+    process), which it refuses after the argument and mode checks."""
     L = sfa.lib()
     L.sfa_match_noalloc.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p,
                                     ctypes.c_void_p]
     big = host(W.workload_large(1 << 12)[0])              # 127 states: ~135 B of scratch per tile
     fake = ctypes.c_void_p(1 << 20)                        # never dereferenced
-    # automatic chunks keep the tile count at the resident CTA count, so even
-    # the longest text fits the fixed scratch; longer ones are invalid
+    # texts past 2^40 bytes are invalid; the longest valid one gets as far as
+    # the check for device tables
     assert L.sfa_match_noalloc(big.handle, fake, (1 << 40) + 1, fake, None) == sfa.ERR_INVALID
-    assert L.sfa_match_noalloc(big.handle, fake, 1 << 40, fake, None) in (sfa.ERR_NO_DEVICE, sfa.ERR_HOST_ONLY)
+    assert L.sfa_match_noalloc(big.handle, fake, 1 << 40, fake, None) == sfa.ERR_HOST_ONLY
     assert L.sfa_match_noalloc(big.handle, None, 16, fake, None) == sfa.ERR_INVALID
     assert L.sfa_match_noalloc(big.handle, fake, 16, None, None) == sfa.ERR_INVALID
     sim = host(W.workload_sim_automata()[0])
     assert L.sfa_match_noalloc(sim.handle, fake, 16, fake, None) == sfa.ERR_UNSUPPORTED
-    # a text that fits passes the host checks and then needs a device (and the
-    # handle's device tables)
-    assert L.sfa_match_noalloc(big.handle, fake, 1 << 20, fake, None) in (sfa.ERR_NO_DEVICE, sfa.ERR_HOST_ONLY)
+    # a valid call still needs the handle's device tables
+    assert L.sfa_match_noalloc(big.handle, fake, 1 << 20, fake, None) == sfa.ERR_HOST_ONLY
 
 
 def _kept_dfa(a):

@@ -75,3 +75,29 @@ def test_noalloc_equals_match_twice(sfa):
         stream.synchronize()
         f, acc, c = oracle.dfa_run(d.delta, d.q0, d.accept, t[:1000])
         assert sfa.decode(out)[0] == (f, acc, 0, c)
+
+
+def test_noalloc_allocates_nothing(sfa):
+    """On a fresh handle (no sfa_match call has given it scratch of its own),
+    once a first call has loaded the kernels, further calls leave the
+    device's free memory and torch's pool exactly as they were: the scratch
+    is the fixed array, nothing is allocated on the device."""
+    d, t = W.workload_large(32 << 20)
+    a = sfa.Automaton.from_dfa(d)
+    stream = torch.cuda.Stream()
+    tt = torch.from_numpy(t).cuda()
+    outs = [torch.zeros(16, dtype=torch.uint8, device="cuda") for _ in range(3)]
+    assert noalloc(sfa, a, tt, outs[0], stream) == sfa.OK
+    stream.synchronize()
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    reserved0 = torch.cuda.memory_reserved()
+    for o in outs[1:]:
+        assert noalloc(sfa, a, tt, o, stream) == sfa.OK
+    stream.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    assert torch.cuda.memory_reserved() == reserved0
+    f, acc, c = oracle.dfa_run(d.delta, d.q0, d.accept, t)
+    for o in outs:
+        assert sfa.decode(o)[0] == (f, acc, 0, c)
