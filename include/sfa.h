@@ -52,7 +52,7 @@ typedef struct sfa_batch *sfa_batch_t;
 /* ---- error codes ------------------------------------------------------- */
 #define SFA_OK               0
 #define SFA_ERR_INVALID     -1  /* bad argument: DFA out of range, NULL pointer, size */
-#define SFA_ERR_UNSUPPORTED -2  /* valid but outside the library's limits (e.g. nq > 256) */
+#define SFA_ERR_UNSUPPORTED -2  /* valid but outside the library's limits (e.g. nq > 4095) */
 #define SFA_ERR_OOM         -3  /* host or device allocation failed */
 #define SFA_ERR_CUDA        -4  /* a CUDA runtime call failed */
 #define SFA_ERR_TIMEOUT     -5  /* a device-side bounded wait gave up (see sfa_result.status) */
@@ -96,7 +96,7 @@ typedef struct {
  * sfa_compile -- Alg. 4 (correspondence construction), Sect. V-A.
  *   delta   host, int32[nq * 256], row-major: delta[q*256 + b] is the state
  *           after reading byte b in state q; every entry in [0, nq)
- *   nq      1..256 states
+ *   nq      1..4095 states
  *   q0      initial state, [0, nq)
  *   accept  host, uint8[nq]: nonzero = final state
  *   opts    NULL for defaults
@@ -111,8 +111,14 @@ typedef struct {
  * shared-memory bank conflicts of the kernel's DFA-row lookups (lanes run
  * over bytes drawn uniformly from the bytes that can change a state; about
  * 20-40 ms of host time for 50-160 states).  Numbering never changes a result.
- * Errors: INVALID (range), UNSUPPORTED (nq > 256, or SFA_MODE_SFA forced
- * past the cap), OOM, CUDA, NO_DEVICE.  Every DFA of 1..256 states compiles
+ * With more than 256 reachable states (up to 4095) the ids are 16-bit, the
+ * DFA rows are indexed by byte class, and point mappings {s -> p, every other
+ * state -> z} (z an absorbing non-final state) are not stored: the matcher
+ * follows p through the DFA rows, so only the other non-constant mappings
+ * count against cap_states.  Such handles have no simulation path.
+ * Errors: INVALID (range), UNSUPPORTED (nq > 4095, SFA_MODE_SFA forced past
+ * the cap, more than 256 reachable states past the cap or with
+ * SFA_MODE_SIM), OOM, CUDA, NO_DEVICE.  Every DFA of 1..256 states compiles
  * in SFA_MODE_AUTO (simulation vectors cover up to 256 reachable states).
  */
 int sfa_compile(const int32_t *delta, int32_t nq, int32_t q0, const uint8_t *accept,
@@ -149,9 +155,22 @@ typedef struct {
     uint64_t n_nonconst;      /* of which non-constant mappings */
     uint64_t table_bytes;     /* device bytes of all tables */
     double compile_seconds;   /* host construction time */
+    uint64_t n_stored;        /* non-constant mappings stored as rows; the others
+                                 (point mappings of automata with more than 256
+                                 reachable states) are followed implicitly */
+    uint32_t id_bits;         /* 8: byte state ids (up to 256 reachable states);
+                                 16: up to 4095 */
+    uint32_t placement;       /* SFA_PLACE_* bits: where the kernel reads its tables */
 } sfa_info_t;
 
-/* sfa_info -- fills *out.  Thm. 2 bounds n_sfa_states by n_reachable^n_reachable. */
+#define SFA_PLACE_SMEM_DFA          1u  /* DFA rows (256 byte columns) in shared memory */
+#define SFA_PLACE_SMEM_DFA_CLASSES  2u  /* 16-bit DFA rows over byte classes in shared memory */
+#define SFA_PLACE_GLOBAL_NC         4u  /* non-constant D-SFA rows in global memory (L1/L2) */
+#define SFA_PLACE_SMEM_VECTORS      8u  /* simulation vectors of 128/256 entries in shared memory */
+
+/* sfa_info -- fills *out.  Thm. 2 bounds n_sfa_states by n_reachable^n_reachable.
+ * n_sfa_states counts every D-SFA state reachable from f_I (stored, implicit
+ * point mappings, constants); n_nonconst the non-constant ones among them. */
 int sfa_info(sfa_handle_t h, sfa_info_t *out);
 
 /* sfa_export -- copies one host table of the handle, for inspection and tests.
@@ -165,6 +184,10 @@ int sfa_info(sfa_handle_t h, sfa_info_t *out);
  *   Kept states are renumbered so that the final ones come last; D-SFA id
  *   c < nr is the constant mapping onto state c, id nr + k the k-th
  *   non-constant mapping in discovery order (k = 0 is f_I when nr > 1).
+ *   Handles with 16-bit ids (more than 256 reachable states) have empty DFA
+ *   and MAPS tables and export CDFA16 and MAPS16 instead; their NC entries
+ *   that lead to a point mapping {s -> p, all other states -> the sink} hold
+ *   1 << 29 | s << 12 | p instead of an id.
  *   Writes min(bytes, table size); returns the table size in *size_out.
  */
 #define SFA_TABLE_CLASS 0
@@ -172,6 +195,8 @@ int sfa_info(sfa_handle_t h, sfa_info_t *out);
 #define SFA_TABLE_NC    2
 #define SFA_TABLE_MAPS  3
 #define SFA_TABLE_ORIG  4
+#define SFA_TABLE_CDFA16 5  /* uint16[nr * ncls]  kept DFA over classes (16-bit ids only) */
+#define SFA_TABLE_MAPS16 6  /* uint16[n_stored * nr] stored mappings (16-bit ids only) */
 int sfa_export(sfa_handle_t h, int32_t which, void *dst, size_t bytes, size_t *size_out);
 
 /* sfa_strerror -- static message for an SFA_* code. */
@@ -238,6 +263,28 @@ int sfa_match_continue(sfa_handle_t h, const uint8_t *d_text, uint64_t n, sfa_re
                        sfa_stream_t stream, const sfa_launch_opts *opts);
 
 /*
+ * sfa_match_map -- the mapping of a text slice (Lemma 1, Theorem 3).  For a
+ * slice w of a longer text: d_map[q] = delta^(q, w) for every state q that is
+ * reachable from q0 (caller ids), -1 for the states that are not.  With
+ * sfa_match_continue this splits one text over several processes or
+ * devices: each part computes its slice's mapping; the mappings of the
+ * parts before it, applied in order to q0, give its entering state s; a
+ * result record {final_state = s, count = 0} passed to sfa_match_continue
+ * then gives its count and its final state (Theorem 3: the results do not
+ * depend on where the text was cut).
+ *   d_text, n  the slice (device, any alignment; may be NULL when n = 0)
+ *   d_out      device, one sfa_result: the slice matched from q0, as sfa_match
+ *   d_map      device, int32[nq] (nq as given to sfa_compile)
+ *   opts       launch shape (NULL = automatic); SFA_TILING_WARP is INVALID
+ *              (the mapping is composed from CTA-tile aggregates)
+ * Enqueues the matching kernel, in which every tile also leaves its mapping
+ * in scratch, and one small kernel that composes them, both on `stream`.
+ * Errors as sfa_match_ex, and INVALID for d_map == NULL.
+ */
+int sfa_match_map(sfa_handle_t h, const uint8_t *d_text, uint64_t n, sfa_result *d_out, int32_t *d_map,
+                  sfa_stream_t stream, const sfa_launch_opts *opts);
+
+/*
  * sfa_match_host -- end-to-end form: host text in, host result out.
  *   h_text  host, n bytes (pinned memory gives full copy bandwidth)
  *   h_out   host, one sfa_result
@@ -290,8 +337,9 @@ int sfa_match_noalloc(sfa_handle_t h, const uint8_t *d_text, uint64_t n, sfa_res
  * sfa_batch_create -- plans one persistent launch over k texts, each matched
  * with its own automaton (Theorem 3 applied per text: every text gets its own
  * look-back chain of tiles).
- *   hs       host, k handles (all compiled on the current device, SFA mode;
- *            simulation-mode handles are matched by per-text launches)
+ *   hs       host, k handles (all compiled on the current device; handles
+ *            in simulation mode or with 16-bit state ids are matched by
+ *            per-text launches)
  *   d_texts  host array of k device pointers
  *   lens     host, k lengths
  *   opts     launch shape (NULL = automatic)
@@ -398,7 +446,8 @@ typedef struct {
 /* sfa_server_create -- n automata (handles on the current device; the
  * handles must outlive the server); opts NULL = defaults.  Allocates the
  * arena, the batch plans, streams, events and pinned result buffers
- * (synchronous).  Errors: INVALID, HOST_ONLY, NO_DEVICE, OOM, CUDA. */
+ * (synchronous).  Errors: INVALID, HOST_ONLY, NO_DEVICE, OOM, CUDA, and
+ * UNSUPPORTED for a handle with 16-bit state ids (sfa_info id_bits = 16). */
 int sfa_server_create(const sfa_handle_t *automata, int32_t n, const sfa_server_opts *opts, sfa_server_t *out);
 
 /* sfa_server_submit -- queue one request: automaton index in [0, n), host

@@ -29,14 +29,15 @@ MODE_AUTO, MODE_SFA, MODE_SIM = 0, 1, 2
 COMPILE_HOST_ONLY, COMPILE_NO_BANK_TUNE = 1, 2
 STATUS_OK, STATUS_TIMEOUT = 0, 1
 DEBUG_SKIP_PUBLISH = 1
-TABLE_CLASS, TABLE_DFA, TABLE_NC, TABLE_MAPS, TABLE_ORIG = 0, 1, 2, 3, 4
+TABLE_CLASS, TABLE_DFA, TABLE_NC, TABLE_MAPS, TABLE_ORIG, TABLE_CDFA16, TABLE_MAPS16 = 0, 1, 2, 3, 4, 5, 6
+PLACE_SMEM_DFA, PLACE_SMEM_DFA_CLASSES, PLACE_GLOBAL_NC, PLACE_SMEM_VECTORS = 1, 2, 4, 8
 TILING_AUTO, TILING_CTA, TILING_WARP = 0, 1, 2
 RESULT_BYTES = 16
 
 # every symbol include/sfa.h declares
 EXPORTED = (
     "sfa_compile", "sfa_compile_sample", "sfa_destroy", "sfa_info", "sfa_export", "sfa_strerror",
-    "sfa_match", "sfa_match_ex", "sfa_match_continue", "sfa_match_host",
+    "sfa_match", "sfa_match_ex", "sfa_match_continue", "sfa_match_host", "sfa_match_map",
     "sfa_batch_create", "sfa_batch_launch", "sfa_batch_graph_launch", "sfa_batch_destroy",
     "sfa_match_batch", "sfa_kernel_launch_count", "sfa_match_noalloc",
     "sfa_batch_reserve", "sfa_batch_update", "sfa_batch_update_host",
@@ -60,7 +61,8 @@ class Info(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_uint32), ("nq", ctypes.c_uint32), ("n_reachable", ctypes.c_uint32),
                 ("n_accepting", ctypes.c_uint32), ("ncls", ctypes.c_uint32), ("on_device", ctypes.c_uint32),
                 ("n_sfa_states", ctypes.c_uint64), ("n_nonconst", ctypes.c_uint64),
-                ("table_bytes", ctypes.c_uint64), ("compile_seconds", ctypes.c_double)]
+                ("table_bytes", ctypes.c_uint64), ("compile_seconds", ctypes.c_double),
+                ("n_stored", ctypes.c_uint64), ("id_bits", ctypes.c_uint32), ("placement", ctypes.c_uint32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -117,6 +119,7 @@ def lib():
     L.sfa_match_ex.argtypes = [P, P, u64, P, P, ctypes.POINTER(LaunchOpts)]
     L.sfa_match_continue.argtypes = [P, P, u64, P, P, ctypes.POINTER(LaunchOpts)]
     L.sfa_match_host.argtypes = [P, P, u64, ctypes.POINTER(Result), P, ctypes.POINTER(LaunchOpts)]
+    L.sfa_match_map.argtypes = [P, P, u64, P, P, P, ctypes.POINTER(LaunchOpts)]
     L.sfa_batch_create.argtypes = [P, P, P, i32, ctypes.POINTER(LaunchOpts), ctypes.POINTER(P)]
     L.sfa_batch_launch.argtypes = [P, P, P]
     L.sfa_batch_graph_launch.argtypes = [P, P, P]
@@ -250,7 +253,7 @@ class Automaton:
         size = ctypes.c_size_t()
         _check(lib().sfa_export(self._h, which, None, 0, ctypes.byref(size)), "sfa_export")
         dtype = {TABLE_CLASS: np.uint8, TABLE_DFA: np.uint8, TABLE_NC: np.uint32, TABLE_MAPS: np.uint8,
-                 TABLE_ORIG: np.int32}[which]
+                 TABLE_ORIG: np.int32, TABLE_CDFA16: np.uint16, TABLE_MAPS16: np.uint16}[which]
         buf = np.zeros(size.value // np.dtype(dtype).itemsize, dtype=dtype)
         _check(lib().sfa_export(self._h, which, buf.ctypes.data, buf.nbytes, ctypes.byref(size)), "sfa_export")
         return buf
@@ -285,6 +288,24 @@ class Automaton:
         _check(lib().sfa_match_continue(self._h, ptr, n, _dev_ptr(inout, "inout"), _stream_ptr(stream),
                                         ctypes.byref(o)), "sfa_match_continue")
         return inout
+
+    def match_map(self, text, out=None, map_out=None, stream=None, **launch):
+        """sfa_match_map: the slice's mapping (int32 CUDA tensor of nq entries,
+        caller ids, -1 for states not reachable from q0) and its result from
+        q0.  Returns (out, map_out)."""
+        if out is None:
+            out = empty_results(1, text.device)
+        if map_out is None:
+            import torch
+            map_out = torch.empty(self.nq, dtype=torch.int32, device=text.device)
+        if map_out.numel() < self.nq:
+            raise ValueError("map_out needs nq entries")
+        o = _launch_opts(**launch)
+        n = text.numel()
+        ptr = _dev_ptr(text, "text") if n else 0
+        _check(lib().sfa_match_map(self._h, ptr, n, _dev_ptr(out, "out"), _dev_ptr(map_out, "map_out"),
+                                   _stream_ptr(stream), ctypes.byref(o)), "sfa_match_map")
+        return out, map_out
 
     def match_host(self, text, stream=None, **launch):
         """End to end: host text (numpy uint8, or a pinned CPU tensor) in,

@@ -73,7 +73,9 @@ struct Shape {
     uint64_t ctas_for(uint64_t tiles) const { return wt ? (tiles + threads / 32 - 1) / (threads / 32) : tiles; }
 };
 
-inline int simnq_for(uint32_t nr) { return nr <= 16 ? 16 : (nr <= 32 ? 32 : 64); }
+inline int simnq_for(uint32_t nr) {
+    return nr <= 16 ? 16 : nr <= 32 ? 32 : nr <= 64 ? 64 : nr <= 128 ? 128 : 256;
+}
 
 // scratch layout of a launch over `ntext` texts and `tiles` tiles
 struct ScratchPlan {
@@ -121,6 +123,6 @@ int launch_kernel(const void *k, int threads, size_t smem, uint32_t ctas, int ma
                   sfa_result *out);
 // one text (sfa_match_ex / sfa_match_continue)
 int match_impl(sfa_handle *h, const uint8_t *d_text, uint64_t n, sfa_result *d_out, cudaStream_t s,
-               const sfa_launch_opts *o, bool carry);
+               const sfa_launch_opts *o, bool carry, int32_t *d_map = nullptr);
 
 }  // namespace sfa_impl

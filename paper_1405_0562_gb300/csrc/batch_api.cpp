@@ -109,7 +109,7 @@ int fill_worklist(sfa_batch *b, const sfa_handle_t *hs, const uint8_t *const *d_
     std::map<sfa_handle_t, uint32_t> tab_of;
     for (int32_t i = 0; i < k; ++i) {
         sfa_handle_t h = hs[i];
-        if (h->host.mode == SFA_MODE_SIM) {
+        if (h->host.mode == SFA_MODE_SIM || h->host.wide) {
             b->sim_index.push_back(i);
             b->sim_handle.push_back(h);
             b->sim_text.push_back(d_texts[i]);
@@ -173,8 +173,10 @@ int fill_worklist(sfa_batch *b, const sfa_handle_t *hs, const uint8_t *const *d_
     return SFA_OK;
 }
 
-// simulation-mode texts are matched with their handle's own scratch: size it
-// now, so that launches of the plan (and graph captures) never allocate
+// simulation-mode texts and texts of 16-bit-id automata are matched with
+// their handle's own scratch: size it now, so that launches of the plan (and
+// graph captures) never allocate.  The tile count is bounded above (a text
+// of two levels has up to one more tile per SM than one level would).
 int size_sim_scratch(sfa_batch *b) {
     for (size_t i = 0; i < b->sim_index.size(); ++i) {
         sfa_handle_t h = b->sim_handle[i];
@@ -185,8 +187,9 @@ int size_sim_scratch(sfa_batch *b) {
         d.n = b->sim_len[i];
         d.chunk = ss.chunk;
         const uint64_t c2 = ss.tile_chunks();
-        const uint64_t t = (sfa_dev::num_chunks(d) + c2 - 1) / c2;
-        rc = ensure_scratch(h, plan_scratch(1, t, h->host.nr, t * c2 * h->host.nr).total);
+        const uint64_t t = (sfa_dev::num_chunks(d) + c2 - 1) / c2 + (uint64_t)std::max(ss.sms, 0) + 2;
+        const uint64_t vec = ss.simnq ? t * c2 * h->host.nr : 0;
+        rc = ensure_scratch(h, plan_scratch(1, t, h->host.nr * (h->host.wide ? 2u : 1u), vec).total);
         if (rc) return rc;
     }
     return SFA_OK;
@@ -275,7 +278,7 @@ int sfa_batch_create(const sfa_handle_t *hs, const uint8_t *const *d_texts, cons
     const uint64_t cpt = (uint64_t)b->shape.threads * b->shape.chains;
     uint64_t total_bytes = 0;
     for (int32_t i = 0; i < k; ++i) {
-        if (hs[i]->host.mode == SFA_MODE_SIM) continue;
+        if (hs[i]->host.mode == SFA_MODE_SIM || hs[i]->host.wide) continue;
         b->nr_max = std::max<uint32_t>(b->nr_max, (uint32_t)hs[i]->host.nr);
         total_bytes += lens[i];
     }
@@ -289,7 +292,7 @@ int sfa_batch_create(const sfa_handle_t *hs, const uint8_t *const *d_texts, cons
     }
     uint64_t tiles = 0;
     for (int32_t i = 0; i < k; ++i)
-        if (hs[i]->host.mode != SFA_MODE_SIM) tiles += text_tiles(lens[i], b->chunk, cpt);
+        if (hs[i]->host.mode != SFA_MODE_SIM && !hs[i]->host.wide) tiles += text_tiles(lens[i], b->chunk, cpt);
     if (tiles >= (1ull << 30)) {
         delete b;
         return SFA_ERR_INVALID;

@@ -57,6 +57,173 @@ uint32_t acc_class(const uint8_t *f, int nr, int first_accept) {
 
 namespace {
 
+// Steps 2-4 for more than 256 kept states: 16-bit ids over byte classes, and
+// point mappings {s -> p, all other states -> z}, for an absorbing non-final
+// state z, kept implicit: Alg. 4 does not enqueue them (their successors are
+// again point mappings, or the constant z, one DFA step of p away), and a
+// row entry whose target is one carries NC_POINT | s << 12 | p.  Only the
+// other non-constant mappings are stored (cap applies to them).  The states
+// reachable from f_I are still all counted: the stored ones, the point
+// mappings (pairs (s, p) closed under p -> delta(p, sigma)) and the constants.
+// There is no simulation path for such automata (UNSUPPORTED past the cap).
+int build_wide(const int32_t *delta, int32_t nq, int32_t q0, const uint8_t *accept, uint32_t cap,
+               const std::vector<int32_t> &order, HostTables &T, std::chrono::steady_clock::time_point t0) {
+    const int nr = (int)order.size();
+    T.nq_in = nq;
+    T.nr = nr;
+    T.wide = true;
+    T.mode = SFA_MODE_SFA;
+    T.orig_of.clear();
+    for (int32_t s : order)
+        if (!accept[s]) T.orig_of.push_back(s);
+    T.first_accept = (int32_t)T.orig_of.size();
+    for (int32_t s : order)
+        if (accept[s]) T.orig_of.push_back(s);
+    T.kept_of.assign(nq, -1);
+    for (int32_t i = 0; i < nr; ++i) T.kept_of[T.orig_of[i]] = i;
+    T.q0 = T.kept_of[q0];
+    T.dfa.clear();
+    T.maps.clear();
+    std::vector<uint16_t> d16((size_t)nr * 256);
+    for (int i = 0; i < nr; ++i)
+        for (int b = 0; b < 256; ++b) d16[(size_t)i * 256 + b] = (uint16_t)T.kept_of[delta[(int64_t)T.orig_of[i] * 256 + b]];
+    // byte classes: equal columns of the kept table
+    {
+        std::unordered_map<std::string, int, VecHash> cols;
+        std::string col(2 * (size_t)nr, '\0');
+        T.ncls = 0;
+        for (int b = 0; b < 256; ++b) {
+            for (int i = 0; i < nr; ++i) std::memcpy(&col[2 * (size_t)i], &d16[(size_t)i * 256 + b], 2);
+            auto it = cols.find(col);
+            if (it == cols.end()) it = cols.emplace(col, T.ncls++).first;
+            T.cls[b] = (uint8_t)it->second;
+        }
+    }
+    const int ncls = T.ncls;
+    std::vector<uint8_t> rep(ncls);
+    for (int b = 255; b >= 0; --b) rep[T.cls[b]] = (uint8_t)b;
+    T.cdfa.assign((size_t)nr * ncls, 0);
+    for (int i = 0; i < nr; ++i)
+        for (int c = 0; c < ncls; ++c) T.cdfa[(size_t)i * ncls + c] = d16[(size_t)i * 256 + rep[c]];
+    // the sink: an absorbing non-final kept state
+    T.sink = -1;
+    for (int q = 0; q < T.first_accept && T.sink < 0; ++q) {
+        bool absorbing = true;
+        for (int c = 0; c < ncls && absorbing; ++c) absorbing = T.cdfa[(size_t)q * ncls + c] == q;
+        if (absorbing) T.sink = q;
+    }
+    const int z = T.sink;
+    // Alg. 4 over the stored (neither constant nor point) mappings
+    T.ident = (uint32_t)nr;
+    T.n_nc = 0;
+    T.nc.clear();
+    T.maps16.clear();
+    std::unordered_map<std::string, uint32_t, VecHash> ids;
+    std::string g(2 * (size_t)nr, '\0');
+    std::vector<uint16_t> gv(nr);
+    for (int q = 0; q < nr; ++q) gv[q] = (uint16_t)q;
+    T.maps16.insert(T.maps16.end(), gv.begin(), gv.end());
+    ids.emplace(std::string(reinterpret_cast<const char *>(gv.data()), 2 * (size_t)nr), 0);
+    T.n_nc = 1;
+    for (uint64_t head = 0; head < T.n_nc; ++head) {
+        for (int c = 0; c < ncls; ++c) {
+            const uint16_t *fm = T.maps16.data() + head * nr;
+            int live = 0, src = -1;
+            bool constant = true;
+            for (int q = 0; q < nr; ++q) {
+                gv[q] = T.cdfa[(size_t)fm[q] * ncls + c];
+                constant &= gv[q] == gv[0];
+                if ((int)gv[q] != z) {
+                    ++live;
+                    src = q;
+                }
+            }
+            uint32_t e;
+            if (constant) {
+                e = gv[0];
+            } else if (z >= 0 && live == 1) {
+                e = NC_POINT | (uint32_t)src << WIDE_POINT_SHIFT | gv[src];
+            } else {
+                std::memcpy(&g[0], gv.data(), 2 * (size_t)nr);
+                auto it = ids.find(g);
+                if (it == ids.end()) {
+                    if (T.n_nc >= cap) return SFA_ERR_UNSUPPORTED;
+                    it = ids.emplace(g, (uint32_t)T.n_nc).first;
+                    T.maps16.insert(T.maps16.end(), gv.begin(), gv.end());
+                    ++T.n_nc;
+                }
+                e = (uint32_t)nr + it->second;
+            }
+            T.nc.push_back(e);
+        }
+    }
+    // acceptance class of each target (point mappings: none, the kernel
+    // follows their live state instead)
+    for (uint32_t &e : T.nc) {
+        if (e & NC_POINT) continue;
+        const uint32_t id = e;
+        uint32_t a;
+        if (id < (uint32_t)nr) {
+            a = (int)id >= T.first_accept ? ACC_ALL : ACC_NONE;
+        } else {
+            const uint16_t *f = T.maps16.data() + (size_t)(id - nr) * nr;
+            bool any = false, all = true;
+            for (int q = 0; q < nr; ++q) {
+                const bool fin = f[q] >= T.first_accept;
+                any |= fin;
+                all &= fin;
+            }
+            a = all ? ACC_ALL : (any ? ACC_MIXED : ACC_NONE);
+        }
+        e = id | (a << NC_ACC_SHIFT);
+    }
+    // reachable constants and point mappings
+    std::vector<char> creach(nr, 0);
+    std::vector<int> cstack;
+    auto cmark = [&](int c) {
+        if (!creach[c]) {
+            creach[c] = 1;
+            cstack.push_back(c);
+        }
+    };
+    std::vector<uint64_t> preach(((size_t)nr * nr + 63) / 64, 0);
+    std::vector<uint32_t> pstack;
+    auto pmark = [&](uint32_t s_, uint32_t p_) {
+        const size_t k = (size_t)s_ * nr + p_;
+        if (!(preach[k >> 6] >> (k & 63) & 1)) {
+            preach[k >> 6] |= 1ull << (k & 63);
+            pstack.push_back((uint32_t)k);
+        }
+    };
+    for (uint32_t e : T.nc) {
+        if (e & NC_POINT)
+            pmark((e >> WIDE_POINT_SHIFT) & 0xfffu, e & 0xfffu);
+        else if ((e & NC_ID_MASK) < (uint32_t)nr)
+            cmark((int)(e & NC_ID_MASK));
+    }
+    T.n_points = 0;
+    while (!pstack.empty()) {
+        const uint32_t k = pstack.back();
+        pstack.pop_back();
+        ++T.n_points;
+        const uint32_t s_ = k / nr, p_ = k % nr;
+        for (int c = 0; c < ncls; ++c) {
+            const uint32_t np = T.cdfa[(size_t)p_ * ncls + c];
+            if ((int)np == z) cmark(z);
+            else pmark(s_, np);
+        }
+    }
+    while (!cstack.empty()) {
+        const int c0 = cstack.back();
+        cstack.pop_back();
+        for (int c = 0; c < ncls; ++c) cmark(T.cdfa[(size_t)c0 * ncls + c]);
+    }
+    T.n_const = 0;
+    for (char r : creach) T.n_const += r ? 1 : 0;
+    T.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    return SFA_OK;
+}
+
 // Steps 1-5 with the kept states numbered breadth first (final states last),
 // then renumbered by `renumber` (new id of every such id) when given.
 int build_numbered(const int32_t *delta, int32_t nq, int32_t q0, const uint8_t *accept, uint32_t cap,
@@ -64,7 +231,7 @@ int build_numbered(const int32_t *delta, int32_t nq, int32_t q0, const uint8_t *
     auto t0 = std::chrono::steady_clock::now();
     if (!delta || !accept) return SFA_ERR_INVALID;
     if (nq < 1) return SFA_ERR_INVALID;
-    if (nq > 256) return SFA_ERR_UNSUPPORTED;
+    if (nq > WIDE_MAX_STATES) return SFA_ERR_UNSUPPORTED;
     if (q0 < 0 || q0 >= nq) return SFA_ERR_INVALID;
     for (int64_t i = 0; i < (int64_t)nq * 256; ++i)
         if (delta[i] < 0 || delta[i] >= nq) return SFA_ERR_INVALID;
@@ -85,6 +252,15 @@ int build_numbered(const int32_t *delta, int32_t nq, int32_t q0, const uint8_t *
                 order.push_back(t);
             }
         }
+    if ((int)order.size() > NARROW_MAX_STATES) {
+        if (force_mode == SFA_MODE_SIM) return SFA_ERR_UNSUPPORTED;
+        return build_wide(delta, nq, q0, accept, cap, order, T, t0);
+    }
+    T.wide = false;
+    T.sink = -1;
+    T.cdfa.clear();
+    T.maps16.clear();
+    T.n_points = 0;
     T.nq_in = nq;
     T.nr = (int32_t)order.size();
     T.orig_of.clear();
@@ -221,7 +397,7 @@ int build_tables(const int32_t *delta, int32_t nq, int32_t q0, const uint8_t *ac
                  uint64_t sample_len) {
     auto t0 = std::chrono::steady_clock::now();
     int rc = build_numbered(delta, nq, q0, accept, cap, force_mode, T, nullptr);
-    if (rc || !tune_banks || T.mode != SFA_MODE_SFA || T.nr < 3) return rc;
+    if (rc || !tune_banks || T.mode != SFA_MODE_SFA || T.nr < 3 || T.wide) return rc;
     const std::vector<int32_t> id = bank_numbering(T.dfa, T.nr, T.first_accept, T.q0, sample, sample_len);
     bool moved = false;
     for (int32_t i = 0; i < T.nr; ++i) moved |= id[i] != i;

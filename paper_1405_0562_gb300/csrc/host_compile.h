@@ -11,9 +11,13 @@ namespace sfa_impl {
 enum AccClass : uint32_t { ACC_NONE = 0, ACC_ALL = 1, ACC_MIXED = 2 };
 
 constexpr uint32_t NC_ID_MASK = 0x1fffffffu;   // bit 29 is the device's point flag
+constexpr uint32_t NC_POINT = 1u << 29;
 constexpr int NC_ACC_SHIFT = 30;
 constexpr uint32_t DEFAULT_CAP = 65536;
-constexpr int SIM_MAX_STATES = 64;
+constexpr int SIM_MAX_STATES = 256;
+constexpr int NARROW_MAX_STATES = 256;         // byte-wide state ids
+constexpr int WIDE_MAX_STATES = 4095;          // 16-bit ids; a point entry holds two 12-bit states
+constexpr int WIDE_POINT_SHIFT = 12;
 
 struct HostTables {
     int32_t nq_in = 0;             // states given by the caller
@@ -32,6 +36,15 @@ struct HostTables {
     std::vector<uint8_t> maps;     // [n_nc*nr]   f(q) of each non-constant state
     uint64_t n_const = 0;          // constant mappings reachable from f_I
     double seconds = 0.0;
+    // More than 256 kept states ("wide"): 16-bit ids, a class-indexed DFA,
+    // and point mappings {s -> p, every other state -> sink} never stored:
+    // a row entry whose target is one carries NC_POINT | s << 12 | p.  The
+    // u8 tables above (dfa, maps) are then empty.
+    bool wide = false;
+    int32_t sink = -1;             // wide: the absorbing non-final state, or -1
+    std::vector<uint16_t> cdfa;    // wide: [nr*ncls] kept DFA over classes
+    std::vector<uint16_t> maps16;  // wide: [n_nc*nr] f(q) of each stored non-constant state
+    uint64_t n_points = 0;         // wide: point mappings reachable from f_I (not stored)
 };
 
 // Returns SFA_OK or an SFA_ERR_* code (see sfa.h for the rules).  tune_banks:

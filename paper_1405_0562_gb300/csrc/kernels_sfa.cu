@@ -28,7 +28,15 @@ const void *kernel_for_sfa(int threads, int chains, bool batch) {
     return nullptr;
 }
 
-size_t smem_bytes(int threads, int chains, uint32_t nr_max) {
+size_t smem_bytes(int threads, int chains, uint32_t nr_max, int simnq) {
+    using namespace sfa_dev;
+    // simulation vectors of more than 64 entries live in shared memory after
+    // the common layout (SmemLayout::vec_off)
+    const size_t vec = simnq > 64 ? (size_t)threads * chains * simnq : 0;
+    return smem_bytes_common(threads, chains, nr_max) + vec;
+}
+
+size_t smem_bytes_common(int threads, int chains, uint32_t nr_max) {
     using namespace sfa_dev;
     switch (threads * 8 + chains) {
         case 128 * 8 + 1: return SmemLayout<128, 1>::bytes(nr_max);

@@ -17,7 +17,7 @@ const void *kernel_for_sim(int threads, int chains, int simnq) {
     if (threads == 256 && chains == 1 && simnq == 64) return SIM_K(256, 1, 64);
     if (threads == 128 && chains == 2 && simnq == 16) return SIM_K(128, 2, 16);
     if (threads == 128 && chains == 2 && simnq == 32) return SIM_K(128, 2, 32);
-    return nullptr;
+    return kernel_for_sim_large(threads, chains, simnq);
 }
 
 }  // namespace sfa_impl

@@ -220,6 +220,8 @@ int sfa_server_create(const sfa_handle_t *automata, int32_t n, const sfa_server_
         if (!automata[i]) return SFA_ERR_INVALID;
         if (!automata[i]->on_device) return SFA_ERR_HOST_ONLY;
         if (automata[i]->device != dev) return SFA_ERR_INVALID;
+        // batch plans hold byte-wide state ids
+        if (automata[i]->host.wide) return SFA_ERR_UNSUPPORTED;
         nr_max = std::max<uint32_t>(nr_max, automata[i]->host.nr);
     }
     sfa_server *s = new (std::nothrow) sfa_server;

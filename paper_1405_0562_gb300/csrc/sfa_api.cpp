@@ -97,8 +97,56 @@ uint32_t point_encoding(const HostTables &H, std::vector<uint32_t> &nc, std::vec
     return (uint32_t)z;
 }
 
+// Device tables of a handle with more than 256 kept states: the class table,
+// the class-indexed 16-bit DFA, the non-constant rows (point entries already
+// encoded by the construction), the stored mappings and the id maps.
+int upload_tables_wide(sfa_handle *h) {
+    const auto &H = h->host;
+    const size_t nr = (size_t)H.nr;
+    size_t off_cdfa = 0;
+    size_t off_cls = align_up(off_cdfa + H.cdfa.size() * 2, 256);
+    size_t off_nc = align_up(off_cls + 256, 256);
+    size_t off_maps = align_up(off_nc + H.nc.size() * 4, 256);
+    size_t off_orig = align_up(off_maps + H.maps16.size() * 2, 256);
+    size_t off_kept = align_up(off_orig + nr * 4, 256);
+    size_t total = align_up(off_kept + (size_t)H.nq_in * 4, 256);
+    std::vector<uint8_t> img(total, 0);
+    std::memcpy(img.data() + off_cdfa, H.cdfa.data(), H.cdfa.size() * 2);
+    std::memcpy(img.data() + off_cls, H.cls, 256);
+    if (!H.nc.empty()) std::memcpy(img.data() + off_nc, H.nc.data(), H.nc.size() * 4);
+    if (!H.maps16.empty()) std::memcpy(img.data() + off_maps, H.maps16.data(), H.maps16.size() * 2);
+    std::memcpy(img.data() + off_orig, H.orig_of.data(), nr * 4);
+    std::memcpy(img.data() + off_kept, H.kept_of.data(), (size_t)H.nq_in * 4);
+    CK(cudaMalloc(&h->d_tables, total));
+    cudaError_t e = cudaMemcpy(h->d_tables, img.data(), total, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(h->d_tables);
+        h->d_tables = nullptr;
+        return cuda_err(e);
+    }
+    h->table_bytes = total;
+    Tables &T = h->dev;
+    T = Tables{};
+    T.cdfa = reinterpret_cast<const uint16_t *>(h->d_tables + off_cdfa);
+    T.cls = h->d_tables + off_cls;
+    T.nc = reinterpret_cast<const uint32_t *>(h->d_tables + off_nc);
+    T.maps16 = reinterpret_cast<const uint16_t *>(h->d_tables + off_maps);
+    T.orig_of = reinterpret_cast<const int32_t *>(h->d_tables + off_orig);
+    T.kept_of = reinterpret_cast<const int32_t *>(h->d_tables + off_kept);
+    T.sink = H.sink >= 0 ? (uint32_t)H.sink : sfa_dev::NO_SINK;
+    T.nr = H.nr;
+    T.ncls = H.ncls;
+    T.first_accept = H.first_accept;
+    T.q0 = H.q0;
+    T.ident = H.ident;
+    T.nq_in = H.nq_in;
+    T.mode = H.mode;
+    return SFA_OK;
+}
+
 int upload_tables(sfa_handle *h) {
     const auto &H = h->host;
+    if (H.wide) return upload_tables_wide(h);
     const size_t nr = (size_t)H.nr;
     std::vector<uint32_t> nc, pid;
     const uint32_t sink = point_encoding(H, nc, pid);
@@ -127,6 +175,7 @@ int upload_tables(sfa_handle *h) {
     }
     h->table_bytes = total;
     Tables &T = h->dev;
+    T = Tables{};
     T.dfa = h->d_tables + off_dfa;
     T.cls = h->d_tables + off_cls;
     T.nc = reinterpret_cast<const uint32_t *>(h->d_tables + off_nc);
@@ -168,7 +217,19 @@ Scratch make_scratch(uint8_t *base, const ScratchPlan &p, uint32_t nr_max, uint3
     S.timeout_us = sh.timeout_us;
     S.debug = sh.debug;
     S.total_tiles = tiles;
+    S.map_mode = 0;
+    S.pad_ = 0;
     return S;
+}
+
+// the kernel instance and shared memory of a single-text launch shape
+const void *shape_kernel(const sfa_handle *h, const Shape &sh) {
+    if (h->host.wide) return sh.wt || sh.simnq ? nullptr : kernel_for_wide(sh.threads, sh.chains);
+    return kernel_for(sh.threads, sh.chains, sh.simnq, false, sh.wt);
+}
+size_t shape_smem(const sfa_handle *h, const Shape &sh) {
+    if (h->host.wide) return smem_bytes_wide(sh.threads, sh.chains, (uint32_t)h->host.nr, (uint32_t)h->host.ncls);
+    return smem_bytes(sh.threads, sh.chains, (uint32_t)h->host.nr, sh.simnq);
 }
 
 // launch shape for one text
@@ -176,21 +237,27 @@ int choose_shape(const sfa_handle *h, uint64_t n, const sfa_launch_opts *o, Shap
     const bool sim = h->host.mode == SFA_MODE_SIM;
     sh = Shape();
     sh.simnq = sim ? simnq_for(h->host.nr) : 0;
-    sh.threads = sim ? 128 : 256;
+    // simulation vectors of 128 and 256 entries live in shared memory, which
+    // then allows one or two CTAs per SM: 256 threads keep 8 warps resident
+    sh.threads = sim ? (sh.simnq > 64 ? 256 : 128) : 256;
     sh.chains = sim ? 1 : 2;
     if (!sim) {
         // one chunk per thread; 512-thread CTAs when two fit on an SM (one
         // CTA's scan and look-back then overlap the other's lookups), else
         // the largest CTA whose shared memory fits
         sh.chains = 1;
-        const int b512 = blocks_per_sm(kernel_for(512, 1, 0, false), 512, smem_bytes(512, 1, h->host.nr));
+        Shape s512 = sh;
+        s512.threads = 512;
+        const int b512 = blocks_per_sm(shape_kernel(h, s512), 512, shape_smem(h, s512));
         if (b512 >= 2) {
             sh.threads = 512;
         } else {
             const size_t optin = device_props(h->device).smem_optin;
             sh.threads = 256;
             for (int t : {1024, 512}) {
-                if (optin == 0 || smem_bytes(t, 1, h->host.nr) <= optin) {
+                Shape st = sh;
+                st.threads = t;
+                if (optin == 0 || shape_smem(h, st) <= optin) {
                     sh.threads = t;
                     break;
                 }
@@ -210,7 +277,7 @@ int choose_shape(const sfa_handle *h, uint64_t n, const sfa_launch_opts *o, Shap
     // CTA tiles unless the caller asks for warp tiles (measured slower on the
     // single-text workloads: their look-back and recount do not overlap)
     sh.wt = tiling == SFA_TILING_WARP;
-    if (!kernel_for(sh.threads, sh.chains, sh.simnq, false, sh.wt)) return SFA_ERR_UNSUPPORTED;
+    if (!shape_kernel(h, sh)) return SFA_ERR_UNSUPPORTED;
     const uint64_t cpt = (uint64_t)sh.threads * sh.chains;
     if (o && o->forced_chunks) {
         if (o->forced_chunks > MAX_FORCED) return SFA_ERR_INVALID;
@@ -223,9 +290,8 @@ int choose_shape(const sfa_handle *h, uint64_t n, const sfa_launch_opts *o, Shap
         if (sh.chunk > MAX_CHUNK) return SFA_ERR_INVALID;
         return SFA_OK;
     }
-    const size_t smem = sfa_impl::smem_bytes(sh.threads, sh.chains, h->host.nr);
-    const int bps =
-        blocks_per_sm(sfa_impl::kernel_for(sh.threads, sh.chains, sh.simnq, false, sh.wt), sh.threads, smem);
+    const size_t smem = shape_smem(h, sh);
+    const int bps = blocks_per_sm(shape_kernel(h, sh), sh.threads, smem);
     const uint64_t ctas = (uint64_t)std::max(1, bps) * std::max(1, device_props(h->device).sms);
     sh.auto_chunk = true;
     sh.bps = bps;
@@ -369,10 +435,13 @@ void fill_level_b_map(TextDesc &d, CUtensorMap &map_b) {
 }
 
 int match_impl(sfa_handle *h, const uint8_t *d_text, uint64_t n, sfa_result *d_out, cudaStream_t s,
-               const sfa_launch_opts *o, bool carry) {
+               const sfa_launch_opts *o, bool carry, int32_t *d_map) {
     if (!h || !d_out) return SFA_ERR_INVALID;
     if (!h->on_device) return SFA_ERR_HOST_ONLY;
     if (n > MAX_TEXT || (n > 0 && !d_text)) return SFA_ERR_INVALID;
+    // the slice mapping is composed from CTA-tile aggregates of byte ids
+    if (d_map && o && o->tiling == SFA_TILING_WARP) return SFA_ERR_INVALID;
+    if (d_map && h->host.wide) return SFA_ERR_UNSUPPORTED;
     Shape sh;
     int rc = choose_shape(h, n, o, sh);
     if (rc) return rc;
@@ -394,18 +463,22 @@ int match_impl(sfa_handle *h, const uint8_t *d_text, uint64_t n, sfa_result *d_o
     d.ntiles = (uint32_t)tiles;
     const uint32_t nr = h->host.nr;
     const uint64_t vec = sh.simnq ? tiles * cpt * nr : 0;
-    ScratchPlan p = plan_scratch(1, tiles, nr, vec);
+    // tile aggregates hold one state id per kept state: 2 bytes with 16-bit ids
+    ScratchPlan p = plan_scratch(1, tiles, nr * (h->host.wide ? 2u : 1u), vec);
     rc = ensure_scratch(h, p.total);
     if (rc) return rc;
     CK(cudaMemsetAsync(h->d_scratch, 0, p.zero, s));
     Scratch S = make_scratch(h->d_scratch, p, nr, (uint32_t)tiles, sh);
-    const void *k = sfa_impl::kernel_for(sh.threads, sh.chains, sh.simnq, false, sh.wt);
-    const size_t smem = sfa_impl::smem_bytes(sh.threads, sh.chains, nr);
+    S.map_mode = d_map ? 1u : 0u;
+    const void *k = shape_kernel(h, sh);
+    const size_t smem = shape_smem(h, sh);
     alignas(64) CUtensorMap map, map_b;
     fill_text_map(d, map);
     fill_level_b_map(d, map_b);
-    return launch_kernel(k, sh.threads, smem, (uint32_t)sh.ctas_for(tiles), sh.max_ctas, s, h->dev, d, &map,
-                         &map_b, nullptr, nullptr, nullptr, S, d_out);
+    rc = launch_kernel(k, sh.threads, smem, (uint32_t)sh.ctas_for(tiles), sh.max_ctas, s, h->dev, d, &map,
+                       &map_b, nullptr, nullptr, nullptr, S, d_out);
+    if (rc || !d_map) return rc;
+    return launch_compose_tiles(S.agg, (uint32_t)tiles, nr, h->dev.orig_of, (uint32_t)h->host.nq_in, d_map, s);
 }
 
 void free_handle_device(sfa_handle *h) {
@@ -488,10 +561,17 @@ int sfa_info(sfa_handle_t h, sfa_info_t *out) {
     out->n_accepting = (uint32_t)(H.nr - H.first_accept);
     out->ncls = (uint32_t)H.ncls;
     out->on_device = h->on_device ? 1u : 0u;
-    out->n_nonconst = H.mode == SFA_MODE_SFA ? (H.nr > 1 ? H.n_nc : 0) : 0;
+    out->n_nonconst = H.mode == SFA_MODE_SFA ? (H.nr > 1 ? H.n_nc + H.n_points : 0) : 0;
     out->n_sfa_states = H.mode == SFA_MODE_SFA ? out->n_nonconst + H.n_const : 0;
     out->table_bytes = h->table_bytes;
     out->compile_seconds = H.seconds;
+    out->n_stored = H.mode == SFA_MODE_SFA ? (H.nr > 1 ? H.n_nc : 0) : 0;
+    out->id_bits = H.wide ? 16u : 8u;
+    if (H.mode == SFA_MODE_SIM)
+        out->placement = SFA_PLACE_SMEM_DFA | (simnq_for((uint32_t)H.nr) > 64 ? SFA_PLACE_SMEM_VECTORS : 0u);
+    else
+        out->placement = (H.wide ? SFA_PLACE_SMEM_DFA_CLASSES : SFA_PLACE_SMEM_DFA) |
+                         (out->n_stored ? SFA_PLACE_GLOBAL_NC : 0u);
     return SFA_OK;
 }
 
@@ -506,6 +586,8 @@ int sfa_export(sfa_handle_t h, int32_t which, void *dst, size_t bytes, size_t *s
         case SFA_TABLE_NC: src = H.nc.data(); sz = H.nc.size() * 4; break;
         case SFA_TABLE_MAPS: src = H.maps.data(); sz = H.maps.size(); break;
         case SFA_TABLE_ORIG: src = H.orig_of.data(); sz = H.orig_of.size() * 4; break;
+        case SFA_TABLE_CDFA16: src = H.cdfa.data(); sz = H.cdfa.size() * 2; break;
+        case SFA_TABLE_MAPS16: src = H.maps16.data(); sz = H.maps16.size() * 2; break;
         default: return SFA_ERR_INVALID;
     }
     if (size_out) *size_out = sz;
@@ -540,6 +622,12 @@ int sfa_match_ex(sfa_handle_t h, const uint8_t *d_text, uint64_t n, sfa_result *
 int sfa_match_continue(sfa_handle_t h, const uint8_t *d_text, uint64_t n, sfa_result *d_inout,
                        sfa_stream_t stream, const sfa_launch_opts *opts) {
     return match_impl(h, d_text, n, d_inout, (cudaStream_t)stream, opts, true);
+}
+
+int sfa_match_map(sfa_handle_t h, const uint8_t *d_text, uint64_t n, sfa_result *d_out, int32_t *d_map,
+                  sfa_stream_t stream, const sfa_launch_opts *opts) {
+    if (!d_map) return SFA_ERR_INVALID;
+    return match_impl(h, d_text, n, d_out, (cudaStream_t)stream, opts, false, d_map);
 }
 
 int sfa_match_host(sfa_handle_t h, const uint8_t *h_text, uint64_t n, sfa_result *h_out, sfa_stream_t stream,
@@ -603,35 +691,36 @@ namespace sfa_impl {
 
 namespace {
 
-// Host-side part of sfa_match_noalloc: argument checks, launch shape and the
-// scratch it needs, all decided before any work is enqueued.
+// Host-side part of sfa_match_noalloc: argument checks, the handle's device,
+// the launch shape and the scratch it needs, all decided before any work is
+// enqueued and before the fixed array's address is looked up.  (The shape
+// itself asks the runtime for occupancy figures: those calls enqueue nothing.)
 int plan_into_scratch(sfa_handle_t h, const uint8_t *d_text, uint64_t n, const sfa_result *d_out, size_t cap,
                       Shape &sh, TextDesc &d, ScratchPlan &p) {
     if (!h || !d_out) return SFA_ERR_INVALID;
     if (n > MAX_TEXT || (n > 0 && !d_text)) return SFA_ERR_INVALID;
     if (h->host.mode != SFA_MODE_SFA) return SFA_ERR_UNSUPPORTED;
-    // the automatic shape; if its tiles need more scratch than `cap`, CTA
-    // tiles (at most one per resident CTA with automatic chunks)
-    for (uint32_t tiling : {(uint32_t)SFA_TILING_AUTO, (uint32_t)SFA_TILING_CTA}) {
-        sfa_launch_opts o{};
-        o.tiling = tiling;
-        int rc = choose_shape(h, n, &o, sh);
-        if (rc) return rc;
-        d = TextDesc{};
-        d.text = d_text;
-        d.n = n;
-        d.chunk = sh.chunk;
-        d.forced = 0;
-        d.origin = sfa_dev::text_origin(d_text);
-        const uint64_t cpt = sh.tile_chunks();
-        if (sfa_dev::num_chunks(d) >= (1ull << 31) - 256) continue;
-        uint64_t tiles = plan_two_levels(sh, n, d);
-        if (!tiles) tiles = (sfa_dev::num_chunks(d) + cpt - 1) / cpt;
-        d.ntiles = (uint32_t)tiles;
-        p = plan_scratch(1, tiles, h->host.nr, 0);
-        if (p.total <= cap) return SFA_OK;
-    }
-    return SFA_ERR_SCRATCH_LIMIT;
+    if (!h->on_device) return SFA_ERR_HOST_ONLY;
+    int dev = -1;
+    CK(cudaGetDevice(&dev));
+    if (dev != h->device) return SFA_ERR_INVALID;
+    // the automatic shape: with automatic chunks a text has at most one CTA
+    // tile per resident CTA, whatever its length
+    int rc = choose_shape(h, n, nullptr, sh);
+    if (rc) return rc;
+    d = TextDesc{};
+    d.text = d_text;
+    d.n = n;
+    d.chunk = sh.chunk;
+    d.forced = 0;
+    d.origin = sfa_dev::text_origin(d_text);
+    const uint64_t cpt = sh.tile_chunks();
+    if (sfa_dev::num_chunks(d) >= (1ull << 31) - 256) return SFA_ERR_SCRATCH_LIMIT;
+    uint64_t tiles = plan_two_levels(sh, n, d);
+    if (!tiles) tiles = (sfa_dev::num_chunks(d) + cpt - 1) / cpt;
+    d.ntiles = (uint32_t)tiles;
+    p = plan_scratch(1, tiles, h->host.nr * (h->host.wide ? 2u : 1u), 0);
+    return p.total <= cap ? SFA_OK : SFA_ERR_SCRATCH_LIMIT;
 }
 
 }  // namespace
@@ -651,7 +740,6 @@ int match_into_scratch(sfa_handle_t h, const uint8_t *d_text, uint64_t n, sfa_re
     int rc = plan_into_scratch(h, d_text, n, d_out, cap, sh, d, p);
     if (rc) return rc;
     if (!scratch) return SFA_ERR_INVALID;
-    if (!h->on_device) return SFA_ERR_HOST_ONLY;
     if (h->device != scratch_device) return SFA_ERR_INVALID;
     const uint64_t tiles = d.ntiles;
     const uint32_t nr = h->host.nr;
@@ -659,8 +747,8 @@ int match_into_scratch(sfa_handle_t h, const uint8_t *d_text, uint64_t n, sfa_re
     // text record and the look-back descriptors
     CK(cudaMemsetAsync(scratch, 0, p.zero, s));
     const Scratch S = make_scratch(scratch, p, nr, (uint32_t)tiles, sh);
-    const void *k = kernel_for(sh.threads, sh.chains, 0, false, sh.wt);
-    const size_t smem = smem_bytes(sh.threads, sh.chains, nr);
+    const void *k = shape_kernel(h, sh);
+    const size_t smem = shape_smem(h, sh);
     alignas(64) CUtensorMap map, map_b;
     fill_text_map(d, map);
     fill_level_b_map(d, map_b);

@@ -31,6 +31,7 @@
 #include <cuda.h>
 
 #include <cstdint>
+#include <type_traits>
 
 #include "sfa.h"
 #include "sfa_types.h"
@@ -186,8 +187,38 @@ struct Chain {
 // offset of (state q, byte b) in the shared-memory DFA rows
 __device__ __forceinline__ uint32_t didx(uint32_t q, uint32_t b) { return q * ROWB + b; }
 
+// DFA-row lookups in shared memory: the transitions of the constant
+// mappings, and of the live state of a point mapping.
+//   byte ids (up to 256 kept states): one row of all 256 byte columns per
+//   state, ROWB bytes apart;
+//   16-bit ids (WIDE): one row of ncls 16-bit entries per state, indexed by
+//   the byte's class (the class table is in shared memory too).
+template <bool WIDE>
+struct Rows;
+template <>
+struct Rows<false> {
+    const uint8_t *d;
+    __device__ __forceinline__ uint32_t next(uint32_t q, uint32_t b) const { return d[q * ROWB + b]; }
+};
+template <>
+struct Rows<true> {
+    const uint16_t *d;
+    const uint8_t *cls;
+    uint32_t ncls;
+    __device__ __forceinline__ uint32_t next(uint32_t q, uint32_t b) const { return d[q * ncls + cls[b]]; }
+};
+
+// Fields of a point-mapping entry NC_POINT | s << PT_SHIFT | p: byte ids
+// carry 8-bit states, 16-bit ids 12-bit ones.
+template <bool WIDE>
+struct Pt {
+    static constexpr uint32_t SHIFT = WIDE ? 12u : 8u;
+    static constexpr uint32_t MASK = (1u << SHIFT) - 1u;
+    static constexpr uint32_t KEEP = NC_POINT | ((1u << (2 * SHIFT)) - 1u);   // the flag and both fields
+};
+
 // one symbol of Alg. 5 in the D-SFA: f <- delta_s[f, sigma].
-// Point mappings {s -> p, others -> sink}: f = NC_POINT | s << 8 | p, and
+// Point mappings {s -> p, others -> sink}: f = NC_POINT | s << SHIFT | p, and
 // f . delta^sigma = {s -> delta(p, sigma), others -> sink} is one DFA-row
 // lookup.  Entering one sets the last mixed position to the entering byte,
 // so that pass 2 reruns the DFA up to there; after it cnt counts the final
@@ -195,25 +226,27 @@ __device__ __forceinline__ uint32_t didx(uint32_t q, uint32_t b) { return q * RO
 // other entering state the chunk is in the non-final sink).  A chunk stays a
 // point mapping to its end, also once p is the sink (then {s -> sink} is
 // the constant sink).
-__device__ __forceinline__ void sfa_step(Chain &s, uint32_t b, int32_t j, const uint8_t *s_dfa,
+template <bool WIDE>
+__device__ __forceinline__ void sfa_step(Chain &s, uint32_t b, int32_t j, const Rows<WIDE> &R,
                                          const uint8_t *s_cls, const uint32_t *nc, uint32_t nr,
                                          uint32_t ncls, uint32_t first_accept) {
+    using P = Pt<WIDE>;
     if (s.f & NC_POINT) {
-        const uint32_t p = s_dfa[didx(s.f & 0xffu, b)];
+        const uint32_t p = R.next(s.f & P::MASK, b);
         s.cnt += p >= first_accept;
-        s.f = (s.f & ~0xffu) | p;
+        s.f = (s.f & ~P::MASK) | p;
     } else if (s.f >= nr) {
         const uint32_t e = __ldg(nc + (size_t)(s.f - nr) * ncls + s_cls[b]);
         // the class bits, without divergent branches
         const uint32_t a = e >> 30;
         const bool pt = (e & NC_POINT) != 0u;
         const bool mark = a == ACC_MIXED || pt;
-        s.f = e & (pt ? (NC_POINT | 0xffffu) : NC_ID_MASK);
+        s.f = e & (pt ? P::KEEP : NC_ID_MASK);
         s.cnt += a == ACC_ALL;
         s.lm = mark ? j : s.lm;
         s.snap = mark ? s.cnt : s.snap;
     } else {
-        s.f = s_dfa[didx(s.f, b)];
+        s.f = R.next(s.f, b);
         s.cnt += s.f >= first_accept;
     }
 }
@@ -227,20 +260,22 @@ __device__ __forceinline__ uint32_t chunk_count_after(const Chain &c, uint32_t v
 }
 
 // 4 symbols of a constant-state chunk, keeping the largest state seen
-__device__ __forceinline__ void dfa_word_max(uint32_t &q, uint32_t &m, uint32_t w, const uint8_t *s_dfa) {
+template <bool WIDE>
+__device__ __forceinline__ void dfa_word_max(uint32_t &q, uint32_t &m, uint32_t w, const Rows<WIDE> &R) {
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-        q = s_dfa[q * ROWB + __byte_perm(w, 0, 0x4440 | j)];
+        q = R.next(q, __byte_perm(w, 0, 0x4440 | j));
         m = max(m, q);
     }
 }
 
 // 4 symbols (one text word) of a constant-state chunk: the DFA row lookups
-__device__ __forceinline__ void dfa_word(uint32_t &q, uint32_t &cnt, uint32_t w, const uint8_t *s_dfa,
+template <bool WIDE>
+__device__ __forceinline__ void dfa_word(uint32_t &q, uint32_t &cnt, uint32_t w, const Rows<WIDE> &R,
                                          uint32_t first_accept) {
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-        q = s_dfa[q * ROWB + __byte_perm(w, 0, 0x4440 | j)];
+        q = R.next(q, __byte_perm(w, 0, 0x4440 | j));
         cnt += q >= first_accept;
     }
 }
@@ -258,10 +293,23 @@ enum : uint32_t { SIM_FULL = 0, SIM_COMPACT = 1, SIM_CONST = 2 };
 
 template <int NQ>
 struct SimChain {
-    uint32_t w[NQ / 4];   // SIM_FULL: T[q]; SIM_COMPACT: slot of T[q]
+    // Vectors of up to 64 entries stay in registers (w); longer ones live in
+    // shared memory (ws), word i of this thread at ws[32 * i]: the 32 lanes
+    // of a warp touch word i of their own vectors in 32 distinct banks.
+    static constexpr bool SMEM = NQ > 64;
+    uint32_t w[SMEM ? 1 : NQ / 4];   // SIM_FULL: T[q]; SIM_COMPACT: slot of T[q]
+    uint32_t *ws;
     uint32_t u0, u1;      // SIM_COMPACT: U[0..7] (slots past d repeat U[0])
     uint32_t d;           // SIM_COMPACT: number of distinct values
     uint32_t mode;
+    __device__ __forceinline__ uint32_t get(int i) const {
+        if constexpr (SMEM) return ws[32 * i];
+        else return w[i];
+    }
+    __device__ __forceinline__ void set(int i, uint32_t v) {
+        if constexpr (SMEM) ws[32 * i] = v;
+        else w[i] = v;
+    }
 };
 
 // the successors of four packed states on byte b, packed
@@ -299,12 +347,22 @@ __device__ __forceinline__ void sim_byte(SimChain<NQ> &T, Chain &s, uint32_t b, 
     if (T.mode == SIM_FULL) {
         mn = 0xffffffffu;
         mx = 0;
+        if constexpr (SimChain<NQ>::SMEM) {
+#pragma unroll 4
+            for (int i = 0; i < NQ / 4; ++i) {
+                const uint32_t y = step4(T.ws[32 * i], b, s_dfa);
+                T.ws[32 * i] = y;
+                mn = __vminu4(mn, y);
+                mx = __vmaxu4(mx, y);
+            }
+        } else {
 #pragma unroll
-        for (int i = 0; i < NQ / 4; ++i) {
-            const uint32_t y = step4(T.w[i], b, s_dfa);
-            T.w[i] = y;
-            mn = __vminu4(mn, y);
-            mx = __vmaxu4(mx, y);
+            for (int i = 0; i < NQ / 4; ++i) {
+                const uint32_t y = step4(T.w[i], b, s_dfa);
+                T.w[i] = y;
+                mn = __vminu4(mn, y);
+                mx = __vmaxu4(mx, y);
+            }
         }
     } else {
         T.u0 = step4(T.u0, b, s_dfa);
@@ -315,60 +373,131 @@ __device__ __forceinline__ void sim_byte(SimChain<NQ> &T, Chain &s, uint32_t b, 
     acc_update(s, mn, mx, j, first_accept);
 }
 
-__device__ __forceinline__ uint32_t rank64(uint64_t m, uint32_t v) {
-    return (uint32_t)__popcll(m & ((1ull << v) - 1ull));
-}
-// the (at most 8) values of a mask in ascending order, padded with the first
-__device__ __forceinline__ void mask_values(uint64_t m, uint32_t &u0, uint32_t &u1) {
-    const uint32_t first = (uint32_t)__ffsll((long long)m) - 1u;
-    uint32_t v[8];
+// The set of distinct values of a chunk vector (state ids < NQ), as a bit
+// mask of NQ bits in 64-bit words.  Register arrays are only indexed by
+// compile-time constants (a value's word is selected, not addressed), so the
+// mask stays in registers for every NQ.
+template <int NQ>
+struct VSet {
+    static constexpr int W = NQ <= 64 ? 1 : NQ / 64;
+    uint64_t m[W];
+    __device__ __forceinline__ void clear() {
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
-        if (m) {
-            v[k] = (uint32_t)__ffsll((long long)m) - 1u;
-            m &= m - 1ull;
+        for (int w = 0; w < W; ++w) m[w] = 0;
+    }
+    __device__ __forceinline__ void add(uint32_t v) {
+        if (W == 1) {
+            m[0] |= 1ull << v;
         } else {
-            v[k] = first;
+            const uint64_t bit = 1ull << (v & 63u);
+#pragma unroll
+            for (int w = 0; w < W; ++w) m[w] |= (v >> 6) == (uint32_t)w ? bit : 0ull;
         }
     }
-    u0 = v[0] | (v[1] << 8) | (v[2] << 16) | (v[3] << 24);
-    u1 = v[4] | (v[5] << 8) | (v[6] << 16) | (v[7] << 24);
-}
+    __device__ __forceinline__ int count() const {
+        int c = 0;
+#pragma unroll
+        for (int w = 0; w < W; ++w) c += __popcll(m[w]);
+        return c;
+    }
+    // number of values in the set below v
+    __device__ __forceinline__ uint32_t rank(uint32_t v) const {
+        if (W == 1) return (uint32_t)__popcll(m[0] & ((1ull << v) - 1ull));
+        const uint32_t wv = v >> 6;
+        const uint64_t below = (1ull << (v & 63u)) - 1ull;
+        uint32_t r = 0;
+#pragma unroll
+        for (int w = 0; w < W; ++w)
+            r += (uint32_t)w < wv ? (uint32_t)__popcll(m[w]) : ((uint32_t)w == wv ? (uint32_t)__popcll(m[w] & below) : 0u);
+        return r;
+    }
+    // the smallest value (the set is not empty)
+    __device__ __forceinline__ uint32_t first() const {
+        uint32_t v = 0xffffffffu;
+#pragma unroll
+        for (int w = W - 1; w >= 0; --w)
+            if (m[w]) v = 64u * w + (uint32_t)__ffsll((long long)m[w]) - 1u;
+        return v;
+    }
+    // the (at most 8) values in ascending order, four per word, padded with
+    // the first
+    __device__ __forceinline__ void values8(uint32_t &u0, uint32_t &u1) const {
+        uint64_t mm[W];
+#pragma unroll
+        for (int w = 0; w < W; ++w) mm[w] = m[w];
+        const uint32_t f = first();
+        uint32_t v[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            uint32_t x = 0xffffffffu;
+#pragma unroll
+            for (int w = 0; w < W; ++w)
+                if (x == 0xffffffffu && mm[w]) {
+                    x = 64u * w + (uint32_t)__ffsll((long long)mm[w]) - 1u;
+                    mm[w] &= mm[w] - 1ull;
+                }
+            v[k] = x == 0xffffffffu ? f : x;
+        }
+        u0 = v[0] | (v[1] << 8) | (v[2] << 16) | (v[3] << 24);
+        u1 = v[4] | (v[5] << 8) | (v[6] << 16) | (v[7] << 24);
+    }
+    // the ranks of the four values packed in x, packed
+    __device__ __forceinline__ uint32_t rank4(uint32_t x) const {
+        return rank(x & 0xffu) | (rank((x >> 8) & 0xffu) << 8) | (rank((x >> 16) & 0xffu) << 16) |
+               (rank(x >> 24) << 24);
+    }
+};
+
 // selector of __byte_perm that picks U[slot] for the four slots of a word
 __device__ __forceinline__ uint32_t slots_sel(uint32_t x) {
     return (x & 0x7u) | ((x >> 4) & 0x70u) | ((x >> 8) & 0x700u) | ((x >> 12) & 0x7000u);
 }
 
-// re-examine the representation (every 16 bytes); kept states are < 64
+// re-examine the representation (every 16 bytes)
 template <int NQ>
 __device__ __forceinline__ void sim_compact(SimChain<NQ> &T, Chain &s) {
     if (T.mode == SIM_FULL) {
-        uint64_t m = 0;
+        VSet<NQ> m;
+        m.clear();
+        if constexpr (SimChain<NQ>::SMEM) {
+#pragma unroll 4
+            for (int i = 0; i < NQ / 4; ++i) {
+                const uint32_t x = T.ws[32 * i];
 #pragma unroll
-        for (int i = 0; i < NQ / 4; ++i)
+                for (int k = 0; k < 4; ++k) m.add((x >> (8 * k)) & 0xffu);
+            }
+        } else {
 #pragma unroll
-            for (int k = 0; k < 4; ++k) m |= 1ull << ((T.w[i] >> (8 * k)) & 0xffu);
-        const int dd = __popcll(m);
+            for (int i = 0; i < NQ / 4; ++i)
+#pragma unroll
+                for (int k = 0; k < 4; ++k) m.add((T.w[i] >> (8 * k)) & 0xffu);
+        }
+        const int dd = m.count();
         if (dd == 1) {
             T.mode = SIM_CONST;
-            s.f = (uint32_t)__ffsll((long long)m) - 1u;
+            s.f = m.first();
             return;
         }
         if (dd > 8) return;
+        if constexpr (SimChain<NQ>::SMEM) {
+#pragma unroll 4
+            for (int i = 0; i < NQ / 4; ++i) T.ws[32 * i] = m.rank4(T.ws[32 * i]);
+        } else {
 #pragma unroll
-        for (int i = 0; i < NQ / 4; ++i) {
-            const uint32_t x = T.w[i];
-            T.w[i] = rank64(m, x & 0xffu) | (rank64(m, (x >> 8) & 0xffu) << 8) |
-                     (rank64(m, (x >> 16) & 0xffu) << 16) | (rank64(m, x >> 24) << 24);
+            for (int i = 0; i < NQ / 4; ++i) T.w[i] = m.rank4(T.w[i]);
         }
-        mask_values(m, T.u0, T.u1);
+        m.values8(T.u0, T.u1);
         T.d = (uint32_t)dd;
         T.mode = SIM_COMPACT;
     } else if (T.mode == SIM_COMPACT) {
-        uint64_t m = 0;
+        VSet<NQ> m;
+        m.clear();
 #pragma unroll
-        for (int k = 0; k < 4; ++k) m |= (1ull << ((T.u0 >> (8 * k)) & 0xffu)) | (1ull << ((T.u1 >> (8 * k)) & 0xffu));
-        const int dd = __popcll(m);
+        for (int k = 0; k < 4; ++k) {
+            m.add((T.u0 >> (8 * k)) & 0xffu);
+            m.add((T.u1 >> (8 * k)) & 0xffu);
+        }
+        const int dd = m.count();
         if (dd == 1) {
             T.mode = SIM_CONST;
             s.f = T.u0 & 0xffu;
@@ -376,13 +505,15 @@ __device__ __forceinline__ void sim_compact(SimChain<NQ> &T, Chain &s) {
         }
         if ((uint32_t)dd == T.d) return;
         // old slot k moves to the rank of U[k] among the values left
-        const uint32_t n0 = rank64(m, T.u0 & 0xffu) | (rank64(m, (T.u0 >> 8) & 0xffu) << 8) |
-                            (rank64(m, (T.u0 >> 16) & 0xffu) << 16) | (rank64(m, T.u0 >> 24) << 24);
-        const uint32_t n1 = rank64(m, T.u1 & 0xffu) | (rank64(m, (T.u1 >> 8) & 0xffu) << 8) |
-                            (rank64(m, (T.u1 >> 16) & 0xffu) << 16) | (rank64(m, T.u1 >> 24) << 24);
+        const uint32_t n0 = m.rank4(T.u0), n1 = m.rank4(T.u1);
+        if constexpr (SimChain<NQ>::SMEM) {
+#pragma unroll 4
+            for (int i = 0; i < NQ / 4; ++i) T.ws[32 * i] = __byte_perm(n0, n1, slots_sel(T.ws[32 * i]));
+        } else {
 #pragma unroll
-        for (int i = 0; i < NQ / 4; ++i) T.w[i] = __byte_perm(n0, n1, slots_sel(T.w[i]));
-        mask_values(m, T.u0, T.u1);
+            for (int i = 0; i < NQ / 4; ++i) T.w[i] = __byte_perm(n0, n1, slots_sel(T.w[i]));
+        }
+        m.values8(T.u0, T.u1);
         T.d = (uint32_t)dd;
     }
 }
@@ -390,30 +521,40 @@ __device__ __forceinline__ void sim_compact(SimChain<NQ> &T, Chain &s) {
 // the four entries T[4i..4i+3] of a non-constant chain
 template <int NQ>
 __device__ __forceinline__ uint32_t sim_word(const SimChain<NQ> &T, int i) {
-    return T.mode == SIM_FULL ? T.w[i] : __byte_perm(T.u0, T.u1, slots_sel(T.w[i]));
+    const uint32_t x = T.get(i);
+    return T.mode == SIM_FULL ? x : __byte_perm(T.u0, T.u1, slots_sel(x));
 }
 
 // mapping applied to a state: constant ids are their own value
 __device__ __forceinline__ uint32_t apply_map(uint32_t f, uint32_t v, const uint8_t *mtab, uint32_t nr) {
     return f < nr ? f : (uint32_t)mtab[(size_t)(f - nr) * nr + v];
 }
+// 16-bit ids: a chunk may also end as a point mapping {s -> p, others ->
+// sink}, kept in its encoded form (point mappings are not stored)
+__device__ __forceinline__ uint32_t apply_map(uint32_t f, uint32_t v, const uint16_t *mtab, uint32_t nr,
+                                              uint32_t sink) {
+    if (f < nr) return f;
+    if (f & NC_POINT) return v == ((f >> Pt<true>::SHIFT) & Pt<true>::MASK) ? (f & Pt<true>::MASK) : sink;
+    return mtab[(size_t)(f - nr) * nr + v];
+}
 
 // Alg. 2 from state q over [p, e) of the text, counting final states
+template <bool WIDE>
 __device__ __forceinline__ uint32_t dfa_count(const uint8_t *text, uint64_t p, uint64_t e, uint32_t q,
-                                              const uint8_t *s_dfa, uint32_t first_accept) {
+                                              const Rows<WIDE> &R, uint32_t first_accept) {
     uint32_t c = 0;
     while (p < e && (reinterpret_cast<uintptr_t>(text + p) & 15)) {
-        q = s_dfa[didx(q, text[p])];
+        q = R.next(q, text[p]);
         c += q >= first_accept;
         ++p;
     }
     // 16-byte words, the next two loaded while the current two are counted
     // (a long rerun reads its text from HBM)
     auto word16 = [&](const uint4 &v) {
-        dfa_word(q, c, v.x, s_dfa, first_accept);
-        dfa_word(q, c, v.y, s_dfa, first_accept);
-        dfa_word(q, c, v.z, s_dfa, first_accept);
-        dfa_word(q, c, v.w, s_dfa, first_accept);
+        dfa_word<WIDE>(q, c, v.x, R, first_accept);
+        dfa_word<WIDE>(q, c, v.y, R, first_accept);
+        dfa_word<WIDE>(q, c, v.z, R, first_accept);
+        dfa_word<WIDE>(q, c, v.w, R, first_accept);
     };
     if (p + 32 <= e) {
         uint4 v0 = ldg128(text + p), v1 = ldg128(text + p + 16);
@@ -430,7 +571,7 @@ __device__ __forceinline__ uint32_t dfa_count(const uint8_t *text, uint64_t p, u
     }
     for (; p + 16 <= e; p += 16) word16(ldg128(text + p));
     for (; p < e; ++p) {
-        q = s_dfa[didx(q, text[p])];
+        q = R.next(q, text[p]);
         c += q >= first_accept;
     }
     return c;
@@ -443,9 +584,11 @@ __device__ __forceinline__ uint32_t dfa_count(const uint8_t *text, uint64_t p, u
 // tile (with carry: the previous call's final state, Lemma 1), else the
 // decoupled look-back: walk back to the nearest inclusive prefix, then apply
 // the aggregates in between in order.
+template <bool WIDE = false>
 __device__ __forceinline__ uint32_t tile_entering_state(const Scratch &S, const Tables &T, const TextDesc &d,
                                                         const sfa_result *out, TextState *ts, uint32_t gt,
                                                         uint32_t local, uint32_t nr, uint32_t nr_max) {
+    using SID = typename std::conditional<WIDE, uint16_t, uint8_t>::type;
     if (local == 0) {
         if (!d.carry) return T.q0;
         const sfa_result prev = out[d.out_index];
@@ -472,7 +615,7 @@ __device__ __forceinline__ uint32_t tile_entering_state(const Scratch &S, const 
             v = (uint32_t)(wi & 0xffffffffu);
             if (v >= nr) v = 0;
         } else {
-            v = S.agg[(size_t)i * nr_max + v];
+            v = reinterpret_cast<const SID *>(S.agg)[(size_t)i * nr_max + v];
         }
     }
     return v;
@@ -543,8 +686,8 @@ __device__ __noinline__ void resolve_deferred(Misc *m, const Scratch &S, const T
 
 // ---------------------------------------------------------------------------
 // the persistent kernel
-//   SIMNQ = 0: D-SFA mode; SIMNQ = 16/32/64: simulation mode with vectors of
-//   that many entries (the kept states, padded)
+//   SIMNQ = 0: D-SFA mode; SIMNQ = 16/32/64/128/256: simulation mode with
+//   vectors of that many entries (the kept states, padded)
 //   BATCH: tables and texts come from device arrays, else from `tab`/`desc`
 //   WT: warp tiles.  Every warp takes its own tiles of 32 chunks, publishes
 //   its own look-back descriptor and finishes its own tiles, with no CTA
@@ -562,35 +705,52 @@ constexpr int min_ctas_per_sm() {
     return BATCH && SIMNQ == 0 && CH == 1 && THREADS <= 1024 ? 1024 / THREADS : 0;
 }
 
-template <int THREADS, int CH, int SIMNQ, bool BATCH, bool WT = false>
+//   WIDE: 16-bit state ids (more than 256 kept states): class-indexed DFA
+//   rows, point mappings never stored (kept encoded to the chunk's end).
+//   Single texts, CTA tiles, D-SFA mode.
+template <int THREADS, int CH, int SIMNQ, bool BATCH, bool WT = false, bool WIDE = false>
 __global__ void __launch_bounds__(THREADS, (min_ctas_per_sm<THREADS, CH, SIMNQ, BATCH>()))
     sfa_match_kernel(Tables tab, TextDesc desc, const __grid_constant__ CUtensorMap tmap,
                      const __grid_constant__ CUtensorMap tmap_b, const Tables *tabs, const TextDesc *descs,
                      const uint32_t *tile_text, Scratch S, sfa_result *out) {
-    using L = SmemLayout<THREADS, CH>;
+    using L = SmemLayout<THREADS, CH, SIMNQ, WIDE>;
+    using SID = typename std::conditional<WIDE, uint16_t, uint8_t>::type;   // a state in a vector
+    using P = Pt<WIDE>;
     constexpr int CPT = L::CPT, NW = L::NW, G = L::G;
     static_assert(!WT || (!BATCH && CH == 1), "warp tiles: one text, one chunk per thread");
+    static_assert(!WIDE || (!WT && !BATCH && SIMNQ == 0), "16-bit ids: single texts, CTA tiles, D-SFA mode");
     constexpr int NQ = SIMNQ > 0 ? SIMNQ : 4;
+    constexpr uint32_t NO_PT = WIDE ? 0xffffu : 0xffu;   // "no point source" in the extra rows
     extern __shared__ __align__(128) uint8_t smem[];
     const uint32_t nr_max = S.nr_max;
+    const uint32_t lcls = WIDE ? tab.ncls : 0u;   // class count of the layout (16-bit ids)
     uint8_t *s_dfa = smem + L::dfa_off();
-    uint8_t *s_cls = smem + L::cls_off(nr_max);
-    uint32_t *s_f = reinterpret_cast<uint32_t *>(smem + L::f_off(nr_max));
-    uint32_t *s_gval = reinterpret_cast<uint32_t *>(smem + L::gval_off(nr_max));
-    uint32_t *s_gpre = reinterpret_cast<uint32_t *>(smem + L::gpre_off(nr_max));
-    Misc *s_misc = reinterpret_cast<Misc *>(smem + L::misc_off(nr_max));
-    uint8_t *s_gvec = smem + L::gvec_off(nr_max);
+    uint8_t *s_cls = smem + L::cls_off(nr_max, lcls);
+    uint32_t *s_f = reinterpret_cast<uint32_t *>(smem + L::f_off(nr_max, lcls));
+    uint32_t *s_gval = reinterpret_cast<uint32_t *>(smem + L::gval_off(nr_max, lcls));
+    uint32_t *s_gpre = reinterpret_cast<uint32_t *>(smem + L::gpre_off(nr_max, lcls));
+    Misc *s_misc = reinterpret_cast<Misc *>(smem + L::misc_off(nr_max, lcls));
+    SID *s_gvec = reinterpret_cast<SID *>(smem + L::gvec_off(nr_max, lcls));
+    Rows<WIDE> R;
+    if constexpr (WIDE) {
+        R.d = reinterpret_cast<const uint16_t *>(s_dfa);
+        R.cls = s_cls;
+        R.ncls = tab.ncls;
+    } else {
+        R.d = s_dfa;
+    }
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t lanemask_lt = (1u << lane) - 1u;
     // this warp's stage barriers and staging buffers
-    const uint32_t bar0 = smem_addr(smem + L::bar_off(nr_max)) + (uint32_t)warp * STAGES * 8;
-    uint8_t *s_box = smem + L::stage_off(nr_max) + (size_t)warp * STAGES * CH * BOX;
-    uint8_t *s_extra = smem + L::extra_off(nr_max) + (size_t)warp * STAGES * CH * SLICE;
+    const uint32_t bar0 = smem_addr(smem + L::bar_off(nr_max, lcls)) + (uint32_t)warp * STAGES * 8;
+    uint8_t *s_box = smem + L::stage_off(nr_max, lcls) + (size_t)warp * STAGES * CH * BOX;
+    uint8_t *s_extra = smem + L::extra_off(nr_max, lcls) + (size_t)warp * STAGES * CH * SLICE;
+    SID *s_psrc = reinterpret_cast<SID *>(s_extra);   // point sources after pass 1 ([round][lane])
     // the point source of this lane's chunk of round c (after pass 1)
     auto point_src = [&](int c) -> uint32_t {
-        const uint8_t v = s_extra[c * 32 + lane];
-        return v == (uint8_t)NO_POINT ? NO_POINT : (uint32_t)v;
+        const uint32_t v = s_psrc[c * 32 + lane];
+        return v == NO_PT ? NO_POINT : v;
     };
     if (lane == 0)
         for (int s = 0; s < STAGES; ++s) mbar_init(bar0 + 8 * s, 1);
@@ -600,9 +760,15 @@ __global__ void __launch_bounds__(THREADS, (min_ctas_per_sm<THREADS, CH, SIMNQ, 
     uint32_t loaded = 0xffffffffu;   // table index in shared memory (CTA-uniform)
     // stage the DFA rows (ROWB apart) and the class table; all threads
     auto stage_tables = [&](const Tables &T, uint32_t idx) {
-        const uint32_t *src = reinterpret_cast<const uint32_t *>(T.dfa);
-        for (uint32_t i = tid; i < T.nr * 64; i += THREADS)
-            *reinterpret_cast<uint32_t *>(s_dfa + (i >> 6) * ROWB + (i & 63) * 4) = __ldg(src + i);
+        if constexpr (WIDE) {
+            const uint16_t *src = T.cdfa;
+            uint16_t *dst = reinterpret_cast<uint16_t *>(s_dfa);
+            for (uint32_t i = tid; i < T.nr * T.ncls; i += THREADS) dst[i] = __ldg(src + i);
+        } else {
+            const uint32_t *src = reinterpret_cast<const uint32_t *>(T.dfa);
+            for (uint32_t i = tid; i < T.nr * 64; i += THREADS)
+                *reinterpret_cast<uint32_t *>(s_dfa + (i >> 6) * ROWB + (i & 63) * 4) = __ldg(src + i);
+        }
         if (tid < 16) reinterpret_cast<uint4 *>(s_cls)[tid] = __ldg(reinterpret_cast<const uint4 *>(T.cls) + tid);
         loaded = idx;
         __syncthreads();
@@ -693,6 +859,13 @@ __global__ void __launch_bounds__(THREADS, (min_ctas_per_sm<THREADS, CH, SIMNQ, 
         const CUtensorMap *tmap_p = lvb ? &tmap_b : (d.map ? reinterpret_cast<const CUtensorMap *>(d.map) : &tmap);
         if (BATCH && d.map && d.rows2d && lane == 0) tensormap_acquire(d.map);
         const uint8_t *mtab = SIMNQ ? S.chainvec : T.maps;
+        // a chunk or group mapping applied to a state
+        auto amap = [&](uint32_t f, uint32_t v) -> uint32_t {
+            if constexpr (WIDE)
+                return apply_map(f, v, T.maps16, nr, T.sink);
+            else
+                return apply_map(f, v, mtab, nr);
+        };
         const uintptr_t tbase = reinterpret_cast<uintptr_t>(text);
         // index within the level of this thread's chunk c, and of the first
         // chunk of the warp's 32 in that round
@@ -731,7 +904,10 @@ __global__ void __launch_bounds__(THREADS, (min_ctas_per_sm<THREADS, CH, SIMNQ, 
             ch[c].lm = -1;
             if (SIMNQ) {
                 // T = f_I over the kept states; padding entries follow state 0
-#pragma unroll
+                if constexpr (SimChain<NQ>::SMEM)
+                    V[c].ws = reinterpret_cast<uint32_t *>(smem + L::vec_off(nr_max)) +
+                              ((size_t)(c * NW + warp) * (NQ / 4)) * 32 + lane;
+#pragma unroll 4
                 for (int i = 0; i < NQ / 4; ++i) {
                     uint32_t w = 0;
 #pragma unroll
@@ -739,7 +915,7 @@ __global__ void __launch_bounds__(THREADS, (min_ctas_per_sm<THREADS, CH, SIMNQ, 
                         const uint32_t q = 4 * i + b4;
                         w |= (q < nr ? q : 0u) << (8 * b4);
                     }
-                    V[c].w[i] = w;
+                    V[c].set(i, w);
                 }
                 V[c].u0 = V[c].u1 = 0;
                 V[c].d = 0;
@@ -753,7 +929,7 @@ __global__ void __launch_bounds__(THREADS, (min_ctas_per_sm<THREADS, CH, SIMNQ, 
             if (SIMNQ)
                 sim_byte<NQ>(V[c], ch[c], b, j, s_dfa, A);
             else
-                sfa_step(ch[c], b, j, s_dfa, s_cls, T.nc, nr, T.ncls, A);
+                sfa_step<WIDE>(ch[c], b, j, R, s_cls, T.nc, nr, T.ncls, A);
         };
         auto constant = [&](int c) -> bool { return SIMNQ ? V[c].mode == SIM_CONST : ch[c].f < nr; };
 
@@ -864,21 +1040,21 @@ __global__ void __launch_bounds__(THREADS, (min_ctas_per_sm<THREADS, CH, SIMNQ, 
                     for (int c = 0; c < CH; ++c)
                         if (!guard || (uint32_t)(16 * g) < len[c]) {
                             if (direct[c]) {
-                                dfa_word(q[c], ch[c].cnt, v[c].x, s_dfa, A);
-                                dfa_word(q[c], ch[c].cnt, v[c].y, s_dfa, A);
-                                dfa_word(q[c], ch[c].cnt, v[c].z, s_dfa, A);
-                                dfa_word(q[c], ch[c].cnt, v[c].w, s_dfa, A);
+                                dfa_word<WIDE>(q[c], ch[c].cnt, v[c].x, R, A);
+                                dfa_word<WIDE>(q[c], ch[c].cnt, v[c].y, R, A);
+                                dfa_word<WIDE>(q[c], ch[c].cnt, v[c].z, R, A);
+                                dfa_word<WIDE>(q[c], ch[c].cnt, v[c].w, R, A);
                             } else {
-                                dfa_word_max(q[c], m[c], v[c].x, s_dfa);
-                                dfa_word_max(q[c], m[c], v[c].y, s_dfa);
-                                dfa_word_max(q[c], m[c], v[c].z, s_dfa);
-                                dfa_word_max(q[c], m[c], v[c].w, s_dfa);
+                                dfa_word_max<WIDE>(q[c], m[c], v[c].x, R);
+                                dfa_word_max<WIDE>(q[c], m[c], v[c].y, R);
+                                dfa_word_max<WIDE>(q[c], m[c], v[c].z, R);
+                                dfa_word_max<WIDE>(q[c], m[c], v[c].w, R);
                                 if (m[c] >= A) {
                                     uint32_t qq = ch[c].f;
-                                    dfa_word(qq, ch[c].cnt, v[c].x, s_dfa, A);
-                                    dfa_word(qq, ch[c].cnt, v[c].y, s_dfa, A);
-                                    dfa_word(qq, ch[c].cnt, v[c].z, s_dfa, A);
-                                    dfa_word(qq, ch[c].cnt, v[c].w, s_dfa, A);
+                                    dfa_word<WIDE>(qq, ch[c].cnt, v[c].x, R, A);
+                                    dfa_word<WIDE>(qq, ch[c].cnt, v[c].y, R, A);
+                                    dfa_word<WIDE>(qq, ch[c].cnt, v[c].z, R, A);
+                                    dfa_word<WIDE>(qq, ch[c].cnt, v[c].w, R, A);
                                     ++reps[c];
                                 }
                             }
@@ -902,17 +1078,17 @@ __global__ void __launch_bounds__(THREADS, (min_ctas_per_sm<THREADS, CH, SIMNQ, 
 #pragma unroll
                         for (int c = 0; c < CH; ++c) {
                             const uint32_t w = (i >> 2) == 0 ? v[c].x : (i >> 2) == 1 ? v[c].y : (i >> 2) == 2 ? v[c].z : v[c].w;
-                            q[c] = s_dfa[q[c] * ROWB + __byte_perm(w, 0, 0x4440 | (i & 3))];
+                            q[c] = R.next(q[c], __byte_perm(w, 0, 0x4440 | (i & 3)));
                             m[c] = max(m[c], q[c]);
                         }
 #pragma unroll
                     for (int c = 0; c < CH; ++c) {
                         if (m[c] >= A) {
                             uint32_t qq = ch[c].f;
-                            dfa_word(qq, ch[c].cnt, v[c].x, s_dfa, A);
-                            dfa_word(qq, ch[c].cnt, v[c].y, s_dfa, A);
-                            dfa_word(qq, ch[c].cnt, v[c].z, s_dfa, A);
-                            dfa_word(qq, ch[c].cnt, v[c].w, s_dfa, A);
+                            dfa_word<WIDE>(qq, ch[c].cnt, v[c].x, R, A);
+                            dfa_word<WIDE>(qq, ch[c].cnt, v[c].y, R, A);
+                            dfa_word<WIDE>(qq, ch[c].cnt, v[c].z, R, A);
+                            dfa_word<WIDE>(qq, ch[c].cnt, v[c].w, R, A);
                             ++reps[c];
                         }
                         ch[c].f = q[c];
@@ -942,17 +1118,17 @@ __global__ void __launch_bounds__(THREADS, (min_ctas_per_sm<THREADS, CH, SIMNQ, 
                     if (!SIMNQ && (ch[c].f & NC_POINT) && len[c] == (uint32_t)SLICE) {
                         // a point mapping over a full slice: its live state
                         // through the DFA rows, the slice's 64 bytes unrolled
-                        uint32_t q = ch[c].f & 0xffu, cn = ch[c].cnt;
+                        uint32_t q = ch[c].f & P::MASK, cn = ch[c].cnt;
 #pragma unroll
                         for (int g = 0; g < SLICE / 16; ++g) {
                             const uint4 v = *unit(st, c, g);
-                            dfa_word(q, cn, v.x, s_dfa, A);
-                            dfa_word(q, cn, v.y, s_dfa, A);
-                            dfa_word(q, cn, v.z, s_dfa, A);
-                            dfa_word(q, cn, v.w, s_dfa, A);
+                            dfa_word<WIDE>(q, cn, v.x, R, A);
+                            dfa_word<WIDE>(q, cn, v.y, R, A);
+                            dfa_word<WIDE>(q, cn, v.z, R, A);
+                            dfa_word<WIDE>(q, cn, v.w, R, A);
                         }
                         ch[c].cnt = cn;
-                        ch[c].f = (ch[c].f & ~0xffu) | q;
+                        ch[c].f = (ch[c].f & ~P::MASK) | q;
                         continue;
                     }
                     const int32_t j0 = (int32_t)(ba[c] + (uint64_t)s * SLICE - lo[c]);
@@ -960,22 +1136,22 @@ __global__ void __launch_bounds__(THREADS, (min_ctas_per_sm<THREADS, CH, SIMNQ, 
                         const uint4 v = *unit(st, c, g);
                         if (constant(c)) {
                             uint32_t q = ch[c].f, cn = ch[c].cnt;
-                            dfa_word(q, cn, v.x, s_dfa, A);
-                            dfa_word(q, cn, v.y, s_dfa, A);
-                            dfa_word(q, cn, v.z, s_dfa, A);
-                            dfa_word(q, cn, v.w, s_dfa, A);
+                            dfa_word<WIDE>(q, cn, v.x, R, A);
+                            dfa_word<WIDE>(q, cn, v.y, R, A);
+                            dfa_word<WIDE>(q, cn, v.z, R, A);
+                            dfa_word<WIDE>(q, cn, v.w, R, A);
                             ch[c].f = q;
                             ch[c].cnt = cn;
                         } else if (!SIMNQ && (ch[c].f & NC_POINT)) {
                             // a point mapping: its live state p through the
                             // DFA rows, 16 bytes at a time
-                            uint32_t q = ch[c].f & 0xffu, cn = ch[c].cnt;
-                            dfa_word(q, cn, v.x, s_dfa, A);
-                            dfa_word(q, cn, v.y, s_dfa, A);
-                            dfa_word(q, cn, v.z, s_dfa, A);
-                            dfa_word(q, cn, v.w, s_dfa, A);
+                            uint32_t q = ch[c].f & P::MASK, cn = ch[c].cnt;
+                            dfa_word<WIDE>(q, cn, v.x, R, A);
+                            dfa_word<WIDE>(q, cn, v.y, R, A);
+                            dfa_word<WIDE>(q, cn, v.z, R, A);
+                            dfa_word<WIDE>(q, cn, v.w, R, A);
                             ch[c].cnt = cn;
-                            ch[c].f = (ch[c].f & ~0xffu) | q;
+                            ch[c].f = (ch[c].f & ~P::MASK) | q;
                         } else {
                             const uint32_t ws[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
@@ -996,19 +1172,24 @@ __global__ void __launch_bounds__(THREADS, (min_ctas_per_sm<THREADS, CH, SIMNQ, 
             // a point mapping to the end: its source s kept for pass 2 in
             // the warp's extra rows (idle until the next tile's copies), and
             // its D-SFA id (the constant sink once p is there) for the scan
-            uint32_t ps = NO_POINT;
+            uint32_t ps = NO_PT;
             if (!SIMNQ && (ch[c].f & NC_POINT)) {
-                ps = (ch[c].f >> 8) & 0xffu;
-                const uint32_t p = ch[c].f & 0xffu;
-                ch[c].f = p == T.sink ? p : __ldg(T.pid + ps * nr + p);
+                ps = (ch[c].f >> P::SHIFT) & P::MASK;
+                const uint32_t p = ch[c].f & P::MASK;
+                // byte ids: the stored id of {ps -> p}; 16-bit ids keep the
+                // encoded form (point mappings are not stored)
+                if constexpr (WIDE)
+                    ch[c].f = p == T.sink ? p : ch[c].f;
+                else
+                    ch[c].f = p == T.sink ? p : __ldg(T.pid + ps * nr + p);
             }
-            s_extra[c * 32 + lane] = (uint8_t)ps;
+            s_psrc[c * 32 + lane] = (SID)ps;
             if (SIMNQ) sim_compact<NQ>(V[c], ch[c]);
             if (SIMNQ && V[c].mode != SIM_CONST) {
                 // keep the vector for the scan: id nr + global chunk index
                 const uint64_t gk = WT ? (uint64_t)gt * 32 + lane : (uint64_t)gt * CPT + (uint64_t)c * THREADS + tid;
                 uint8_t *dst = S.chainvec + gk * nr;
-#pragma unroll
+#pragma unroll 4
                 for (int i = 0; i < NQ / 4; ++i) {
                     const uint32_t x = sim_word<NQ>(V[c], i);
 #pragma unroll
@@ -1035,7 +1216,7 @@ __global__ void __launch_bounds__(THREADS, (min_ctas_per_sm<THREADS, CH, SIMNQ, 
                 // after it; an inclusive prefix at once
                 const int lc = 31 - __clz(cm);
                 tval = __shfl_sync(0xffffffffu, fl, lc);
-                for (int i = lc + 1; i < 32; ++i) tval = apply_map(__shfl_sync(0xffffffffu, fl, i), tval, mtab, nr);
+                for (int i = lc + 1; i < 32; ++i) tval = amap(__shfl_sync(0xffffffffu, fl, i), tval);
                 if (lane == 0 && !skip) st_relaxed(st, ST_PREFIX | tval);
             } else {
                 // a |Q|-vector: lanes take the components, every chunk in
@@ -1044,7 +1225,7 @@ __global__ void __launch_bounds__(THREADS, (min_ctas_per_sm<THREADS, CH, SIMNQ, 
                 for (uint32_t qb = 0; qb < nr; qb += 32) {
                     const uint32_t q = qb + lane;
                     uint32_t v = q < nr ? q : 0u;
-                    for (int i = 0; i < 32; ++i) v = apply_map(__shfl_sync(0xffffffffu, fl, i), v, mtab, nr);
+                    for (int i = 0; i < 32; ++i) v = amap(__shfl_sync(0xffffffffu, fl, i), v);
                     if (q < nr) {
                         gv[q] = (uint8_t)v;
                         agg[q] = (uint8_t)v;
@@ -1056,7 +1237,7 @@ __global__ void __launch_bounds__(THREADS, (min_ctas_per_sm<THREADS, CH, SIMNQ, 
             }
             uint32_t s_in = 0, incl = tval;
             if (lane == 0) {
-                s_in = tile_entering_state(S, T, d, out, ts, gt, local, nr, nr_max);
+                s_in = tile_entering_state<WIDE>(S, T, d, out, ts, gt, local, nr, nr_max);
                 if (!cm) {
                     incl = gv[s_in];
                     if (!skip) st_relaxed(st, ST_PREFIX | incl);
@@ -1069,10 +1250,10 @@ __global__ void __launch_bounds__(THREADS, (min_ctas_per_sm<THREADS, CH, SIMNQ, 
             const int j = below ? 31 - __clz(below) : -1;
             uint32_t v = __shfl_sync(0xffffffffu, fl, j < 0 ? 0 : j);
             if (j < 0) v = s_in;
-            for (int i = j + 1; i < lane; ++i) v = apply_map(s_f[warp * 32 + i], v, mtab, nr);
+            for (int i = j + 1; i < lane; ++i) v = amap(s_f[warp * 32 + i], v);
             unsigned long long tsum = ch[0].cnt;
             if (ch[0].lm >= 0)
-                tsum = dfa_count(text, lo[0], lo[0] + (uint64_t)ch[0].lm + 1, v, s_dfa, A) +
+                tsum = dfa_count<WIDE>(text, lo[0], lo[0] + (uint64_t)ch[0].lm + 1, v, R, A) +
                        chunk_count_after(ch[0], v, point_src(0));
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) tsum += __shfl_down_sync(0xffffffffu, tsum, o);
@@ -1098,7 +1279,7 @@ __global__ void __launch_bounds__(THREADS, (min_ctas_per_sm<THREADS, CH, SIMNQ, 
                 // composed with the (non-constant) chunks after it
                 const int lc = 31 - __clz(cm);
                 uint32_t v = __shfl_sync(0xffffffffu, fl, lc);
-                for (int i = lc + 1; i < 32; ++i) v = apply_map(__shfl_sync(0xffffffffu, fl, i), v, mtab, nr);
+                for (int i = lc + 1; i < 32; ++i) v = amap(__shfl_sync(0xffffffffu, fl, i), v);
                 if (lane == 0) s_gval[g] = v;
                 my_gconst |= 1u << c;
             } else {
@@ -1106,8 +1287,8 @@ __global__ void __launch_bounds__(THREADS, (min_ctas_per_sm<THREADS, CH, SIMNQ, 
                 for (uint32_t qb = 0; qb < nr; qb += 32) {
                     const uint32_t q = qb + lane;
                     uint32_t v = q < nr ? q : 0u;
-                    for (int i = 0; i < 32; ++i) v = apply_map(__shfl_sync(0xffffffffu, fl, i), v, mtab, nr);
-                    if (q < nr) s_gvec[(size_t)g * nr + q] = (uint8_t)v;
+                    for (int i = 0; i < 32; ++i) v = amap(__shfl_sync(0xffffffffu, fl, i), v);
+                    if (q < nr) s_gvec[(size_t)g * nr + q] = (SID)v;
                 }
             }
         }
@@ -1124,7 +1305,7 @@ __global__ void __launch_bounds__(THREADS, (min_ctas_per_sm<THREADS, CH, SIMNQ, 
         if (warp == 0) {
             const uint32_t gconst = s_misc->gconst & (G == 32 ? 0xffffffffu : ((1u << G) - 1u));
             uint64_t *st = S.status + gt;
-            uint8_t *agg = S.agg + (size_t)gt * nr_max;
+            SID *agg = reinterpret_cast<SID *>(S.agg) + (size_t)gt * nr_max;
             const bool skip = (S.debug & SFA_DEBUG_SKIP_PUBLISH) && local == 1;
             const bool tconst = gconst != 0;
             uint32_t tval = 0;
@@ -1133,13 +1314,17 @@ __global__ void __launch_bounds__(THREADS, (min_ctas_per_sm<THREADS, CH, SIMNQ, 
                 tval = s_gval[gc];
                 for (int g = gc + 1; g < G; ++g) tval = s_gvec[(size_t)g * nr + tval];
                 if (lane == 0 && !skip) st_relaxed(st, ST_PREFIX | tval);
+                // the slice mapping needs every tile's vector: a constant one
+                // maps every state to tval
+                if (S.map_mode)
+                    for (uint32_t q = lane; q < nr; q += 32) agg[q] = (SID)tval;
             } else {
                 for (uint32_t qb = 0; qb < nr; qb += 32) {
                     const uint32_t q = qb + lane;
                     if (q < nr) {
                         uint32_t v = q;
                         for (int g = 0; g < G; ++g) v = s_gvec[(size_t)g * nr + v];
-                        agg[q] = (uint8_t)v;
+                        agg[q] = (SID)v;
                     }
                 }
                 __threadfence();
@@ -1163,7 +1348,7 @@ __global__ void __launch_bounds__(THREADS, (min_ctas_per_sm<THREADS, CH, SIMNQ, 
                     s_misc->dfr_lm = ch[0].lm;
                     s_misc->dfr_valid = 1;
                 } else {
-                    s_in = tile_entering_state(S, T, d, out, ts, gt, local, nr, nr_max);
+                    s_in = tile_entering_state<WIDE>(S, T, d, out, ts, gt, local, nr, nr_max);
                 }
                 uint32_t incl = tval;
                 if (!tconst) {
@@ -1205,13 +1390,13 @@ __global__ void __launch_bounds__(THREADS, (min_ctas_per_sm<THREADS, CH, SIMNQ, 
             const int j = below ? 31 - __clz(below) : -1;
             uint32_t v = __shfl_sync(0xffffffffu, fl, j < 0 ? 0 : j);
             if (j < 0) v = s_gpre[g];
-            for (int i = j + 1; i < lane; ++i) v = apply_map(s_f[g * 32 + i], v, mtab, nr);
+            for (int i = j + 1; i < lane; ++i) v = amap(s_f[g * 32 + i], v);
             uint32_t cc = ch[c].cnt;
             if (ch[c].lm >= 0) {
                 // the tile's first chunk with a deferred recount: only the
                 // positions after its last mixed one now
                 const bool deferred = DEFER && c == 0 && tid == 0 && s_misc->dfr_valid;
-                cc = (deferred ? 0u : dfa_count(text, lo[c], lo[c] + (uint64_t)ch[c].lm + 1, v, s_dfa, A)) +
+                cc = (deferred ? 0u : dfa_count<WIDE>(text, lo[c], lo[c] + (uint64_t)ch[c].lm + 1, v, R, A)) +
                      chunk_count_after(ch[c], v, point_src(c));
             }
             tsum += cc;

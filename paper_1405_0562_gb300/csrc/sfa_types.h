@@ -36,6 +36,9 @@ struct Tables {
     const int32_t *orig_of;    // [nr]
     const int32_t *kept_of;    // [nq_in]
     const uint32_t *pid;       // [nr*nr] id of the point mapping {s -> p} at s*nr + p (sink != NO_SINK)
+    // more than 256 kept states (16-bit ids): dfa and maps are unused
+    const uint16_t *cdfa;      // [nr*ncls] kept DFA over byte classes
+    const uint16_t *maps16;    // [n_nc*nr]  stored non-constant mappings
     uint32_t nr, ncls, first_accept, q0, ident, nq_in, mode;
     uint32_t sink;             // the sink of the point mappings, or NO_SINK
 };
@@ -97,6 +100,10 @@ struct Scratch {
     uint32_t timeout_us;
     uint32_t debug;
     uint32_t total_tiles;
+    uint32_t map_mode;         // 1: every tile leaves its aggregate as a
+                               // |Q|-vector in agg (constant tiles too), for
+                               // the slice mapping of sfa_match_map
+    uint32_t pad_;
 };
 
 // chunks of a one-level text (the empty text, and one shorter than its
@@ -141,32 +148,45 @@ constexpr int STAGES = 2;
 constexpr int BOX = 32 * SLICE;
 static_assert(SLICE == 64, "the read pattern assumes the 64-byte swizzle");
 
-template <int THREADS, int CH>
+// WIDE: 16-bit state ids; the DFA rows are indexed by byte class (ncls
+// 16-bit entries per state) and the group vectors hold 16-bit states.  Every
+// offset takes the table's state count nr_max and, for WIDE, its class count.
+template <int THREADS, int CH, int SIMNQ = 0, bool WIDE = false>
 struct SmemLayout {
     static constexpr int CPT = THREADS * CH;   // chunks per tile
     static constexpr int NW = THREADS / 32;
     static constexpr int G = CPT / 32;         // groups per tile
+    static constexpr size_t IDB = WIDE ? 2 : 1;   // bytes per state id
     static_assert(G <= 32, "at most 1024 chunks per tile");
     // offsets in bytes from the start of dynamic shared memory
     static SFA_HD size_t a16(size_t x) { return (x + 15) & ~(size_t)15; }
     static SFA_HD size_t dfa_off() { return 0; }
-    static SFA_HD size_t cls_off(uint32_t nr_max) { return a16((size_t)nr_max * ROWB); }
-    static SFA_HD size_t f_off(uint32_t nr_max) { return cls_off(nr_max) + 256; }
-    static SFA_HD size_t gval_off(uint32_t nr_max) { return f_off(nr_max) + CPT * 4; }
-    static SFA_HD size_t gpre_off(uint32_t nr_max) { return gval_off(nr_max) + 32 * 4; }
-    static SFA_HD size_t misc_off(uint32_t nr_max) { return gpre_off(nr_max) + 32 * 4; }
-    static SFA_HD size_t gvec_off(uint32_t nr_max) { return misc_off(nr_max) + 512; }
-    static SFA_HD size_t bar_off(uint32_t nr_max) { return a16(gvec_off(nr_max) + (size_t)G * nr_max); }
+    static SFA_HD size_t cls_off(uint32_t nr_max, uint32_t ncls = 0) {
+        return a16(WIDE ? (size_t)nr_max * ncls * 2 : (size_t)nr_max * ROWB);
+    }
+    static SFA_HD size_t f_off(uint32_t nr_max, uint32_t ncls = 0) { return cls_off(nr_max, ncls) + 256; }
+    static SFA_HD size_t gval_off(uint32_t nr_max, uint32_t ncls = 0) { return f_off(nr_max, ncls) + CPT * 4; }
+    static SFA_HD size_t gpre_off(uint32_t nr_max, uint32_t ncls = 0) { return gval_off(nr_max, ncls) + 32 * 4; }
+    static SFA_HD size_t misc_off(uint32_t nr_max, uint32_t ncls = 0) { return gpre_off(nr_max, ncls) + 32 * 4; }
+    static SFA_HD size_t gvec_off(uint32_t nr_max, uint32_t ncls = 0) { return misc_off(nr_max, ncls) + 512; }
+    static SFA_HD size_t bar_off(uint32_t nr_max, uint32_t ncls = 0) {
+        return a16(gvec_off(nr_max, ncls) + (size_t)G * nr_max * IDB);
+    }
     // boxes: [warp][stage][round] x BOX, 1024-byte aligned (the swizzle
     // pattern repeats every 512 bytes); extra rows: [warp][stage][round] x SLICE
-    static SFA_HD size_t stage_off(uint32_t nr_max) {
-        return (bar_off(nr_max) + (size_t)NW * STAGES * 8 + 1023) & ~(size_t)1023;
+    static SFA_HD size_t stage_off(uint32_t nr_max, uint32_t ncls = 0) {
+        return (bar_off(nr_max, ncls) + (size_t)NW * STAGES * 8 + 1023) & ~(size_t)1023;
     }
-    static SFA_HD size_t extra_off(uint32_t nr_max) {
-        return stage_off(nr_max) + (size_t)NW * STAGES * CH * BOX;
+    static SFA_HD size_t extra_off(uint32_t nr_max, uint32_t ncls = 0) {
+        return stage_off(nr_max, ncls) + (size_t)NW * STAGES * CH * BOX;
     }
-    static SFA_HD size_t bytes(uint32_t nr_max) {
-        return extra_off(nr_max) + (size_t)NW * STAGES * CH * SLICE;
+    // simulation vectors of more than 64 entries: SIMNQ bytes per chunk,
+    // [round][warp][word][lane] (see SimChain)
+    static SFA_HD size_t vec_off(uint32_t nr_max, uint32_t ncls = 0) {
+        return a16(extra_off(nr_max, ncls) + (size_t)NW * STAGES * CH * SLICE);
+    }
+    static SFA_HD size_t bytes(uint32_t nr_max, uint32_t ncls = 0) {
+        return vec_off(nr_max, ncls) + (SIMNQ > 64 ? (size_t)CPT * SIMNQ : 0);
     }
 };
 

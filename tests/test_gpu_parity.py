@@ -381,6 +381,61 @@ def test_forced_simulation_small(name):
         assert gpu_match(a, t, forced_chunks=p) == expect(d, t)
 
 
+@pytest.mark.parametrize("nq", [65, 100, 128, 200, 256])
+def test_simulation_large_random_dfas(nq):
+    """Alg. 3 past 64 states: vectors of 128 and 256 entries in shared
+    memory.  Random complete DFAs over 16 symbols, 1 MiB and 256 MiB, the
+    automatic shape, short chunks (many chunks still a vector at their end,
+    combined through their scratch vectors) and forced chunk counts."""
+    sfa = sfa_mod()
+    d = W.dfa_random(nq, 16, seed=1405004 + nq)
+    a = sfa.Automaton.from_dfa(d)
+    assert a.info()["mode"] == sfa.MODE_SIM
+    t = W.text_uniform(256 << 20, bytes(range(16)), 77 + nq)
+    assert gpu_match(a, t) == expect(d, t)
+    small = t[:(1 << 20) + 7]
+    want = expect(d, small)
+    assert gpu_match(a, small) == want
+    for launch in ({"chunk_bytes": 64}, {"chunk_bytes": 1000}, {"forced_chunks": 37}, {"forced_chunks": 1},
+                   {"block_threads": 128, "chains": 1, "chunk_bytes": 256}):
+        assert gpu_match(a, small, **launch) == want, launch
+
+
+@pytest.mark.parametrize("nq", [100, 200, 256])
+def test_simulation_permutations_never_converge(nq):
+    """A cycle automaton forced into simulation mode: every chunk vector is
+    a rotation to its end (no chunk ever becomes constant), so every chunk
+    is combined through its scratch vector."""
+    sfa = sfa_mod()
+    delta = np.tile((np.arange(nq, dtype=np.int32)[:, None] + 1) % nq, (1, 256))
+    delta[:, ord("b")] = (np.arange(nq, dtype=np.int32) + 2) % nq
+    acc = (np.arange(nq) % 7 == 3).astype(np.uint8)
+    d = W.DFA(delta, 0, acc, b"ab", name=f"cycle{nq}")
+    a = sfa.Automaton.from_dfa(d, mode=sfa.MODE_SIM)
+    t = text_for(d, (1 << 20) + 3, seed=nq)
+    want = expect(d, t)
+    for launch in ({}, {"chunk_bytes": 64}, {"forced_chunks": 64}):
+        assert gpu_match(a, t, **launch) == want, launch
+
+
+def test_full_transformation_6():
+    """The generators of the full transformation monoid T_6 (Fact 2): the
+    D-SFA has 6^6 = 46656 states (under the default cap, so D-SFA mode with
+    its non-constant rows in L2), and the same DFA in simulation mode."""
+    sfa = sfa_mod()
+    d = W.dfa_full_transformation(6)
+    a = sfa.Automaton.from_dfa(d)
+    assert a.info()["mode"] == sfa.MODE_SFA and a.info()["n_sfa_states"] == 6 ** 6
+    s = sfa.Automaton.from_dfa(d, mode=sfa.MODE_SIM)
+    t = text_for(d, (16 << 20) + 5, seed=6)
+    want = expect(d, t)
+    for h in (a, s):
+        assert gpu_match(h, t) == want
+        assert gpu_match(h, t[:100_001], chunk_bytes=64) == expect(d, t[:100_001])
+        for p in (1, 7, 64):
+            assert gpu_match(h, t[:30_001], forced_chunks=p) == expect(d, t[:30_001])
+
+
 # ---------------------------------------------------------------------------
 # streaming (Lemma 1), host path, batches, timeouts
 # ---------------------------------------------------------------------------
@@ -399,6 +454,73 @@ def test_match_continue_pieces(name):
         a.match_continue(tt[bounds[i]:bounds[i + 1]], out, chunk_bytes=64)
     torch.cuda.synchronize()
     assert sfa_mod().decode(out)[0] == expect(d, t)
+
+
+def _oracle_map(d, text):
+    """delta^(q, text) for every state reachable from q0, -1 for the rest
+    (Alg. 2 from each state)."""
+    seen, todo = {d.q0}, [d.q0]
+    while todo:
+        q = todo.pop()
+        for t in np.unique(d.delta[q]):
+            if int(t) not in seen:
+                seen.add(int(t))
+                todo.append(int(t))
+    m = np.full(d.nq, -1, dtype=np.int32)
+    for q in seen:
+        m[q] = oracle.dfa_run(d.delta, d.q0, d.accept, text, start=q)[0]
+    return m
+
+
+@pytest.mark.parametrize("name", ["ac_set", "r5", "rand8", "T4", "kmp", "ab_star", "one_state"])
+def test_match_map_equals_oracle(name):
+    """sfa_match_map: the slice mapping over every kept state (Lemma 1) and
+    the result from q0, for short and long texts (two levels), CTA shapes,
+    forced chunk counts, an unaligned view and the simulation path."""
+    sfa = sfa_mod()
+    d = AUTOMATA[name]()
+    handles = [sfa.Automaton.from_dfa(d)]
+    if name in ("rand8", "T4", "r5"):
+        handles.append(sfa.Automaton.from_dfa(d, mode=sfa.MODE_SIM))
+    base = text_for(d, (24 << 20) + 77, seed=11)
+    dev = torch.from_numpy(base).cuda()
+    for lo, hi in ((0, 0), (0, 1), (3, 4099), (0, 1 << 20), (5, (24 << 20) + 77)):
+        t = base[lo:hi]
+        want_map = _oracle_map(d, t)
+        want = expect(d, t)
+        for a in handles:
+            for launch in ({}, {"chunk_bytes": 64, "block_threads": 128, "chains": 2}, {"forced_chunks": 33}):
+                out, m = a.match_map(dev[lo:hi], **launch)
+                torch.cuda.synchronize()
+                assert sfa.decode(out)[0] == want, (lo, hi, launch)
+                assert np.array_equal(m.cpu().numpy(), want_map), (lo, hi, launch)
+
+
+def test_match_map_then_continue_splits_a_text():
+    """The split of one text on one device: the mappings of the slices
+    before a slice give its entering state; sfa_match_continue from there
+    gives its count; the sum and the last final state are the text's."""
+    from paper_1405_0562_gb300 import split
+    sfa = sfa_mod()
+    for d, t in (W.workload_large(64 << 20), (W.dfa_rn(5), W.text_rn_accepted(8 << 20, 5, 1))):
+        a = sfa.Automaton.from_dfa(d)
+        dev = torch.from_numpy(t).cuda()
+        cuts = [0, 1000, 1000, (3 << 20) + 5, t.size - 17, t.size]
+        maps, outs = [], []
+        for i in range(len(cuts) - 1):
+            o, m = a.match_map(dev[cuts[i]:cuts[i + 1]])
+            maps.append(m.cpu().numpy())
+            outs.append(o)
+        s = split.entering_states(maps, d.q0)
+        total = 0
+        for i in range(len(cuts) - 1):
+            rec = torch.from_numpy(split.result_record(s[i])).cuda()
+            a.match_continue(dev[cuts[i]:cuts[i + 1]], rec)
+            torch.cuda.synchronize()
+            f, acc, st, c = sfa.decode(rec)[0]
+            assert st == 0
+            total += c
+        assert (f, acc, 0, total) == expect(d, t)
 
 
 def test_match_host_pinned_and_pageable():
@@ -492,6 +614,38 @@ def test_full_simulation_4GiB():
         got = sfa_mod().decode(out)[0]
         assert got == expect(d, t), d.name
     del tt
+
+
+def test_text_longer_than_2_32():
+    """Texts of 2^32 + 2^20 + 13 bytes: 64-bit offsets and chunk positions,
+    the two-level split of automatic chunks above 4 GiB, a count above 2^32
+    (the one-state automaton whose every prefix is accepted: count = n), and
+    Lemma 1 streaming with a piece boundary just below and exactly at 2^32.
+    Every field against the oracle's Alg. 2, tolerance 0."""
+    sfa = sfa_mod()
+    n = (1 << 32) + (1 << 20) + 13
+    t = W.workload_sim_text(n)
+    one = AUTOMATA["one_state"]()
+    sim16 = W.workload_sim_automata()[0]
+    d_ac, t_ac = W.workload_large(n)
+    for d, text in ((one, t), (sim16, t), (d_ac, t_ac)):
+        want = expect(d, text)
+        if d is one:
+            assert want == (0, 1, 0, n)
+        a = sfa.Automaton.from_dfa(d)
+        tt = torch.from_numpy(text).cuda()
+        launches = [{}, {"tiling": sfa.TILING_WARP}] if d is not sim16 else [{}]
+        for launch in launches:
+            out = a.match(tt, **launch)
+            torch.cuda.synchronize()
+            assert sfa.decode(out)[0] == want, (d.name, launch)
+        for cut in ((1 << 32) - 7, 1 << 32):
+            out = a.match(tt[:cut])
+            a.match_continue(tt[cut:], out)
+            torch.cuda.synchronize()
+            assert sfa.decode(out)[0] == want, (d.name, cut)
+        del tt
+        torch.cuda.empty_cache()
 
 
 def test_full_batch_4096_texts():

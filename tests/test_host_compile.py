@@ -141,10 +141,33 @@ def test_example1_product_numbering():
 
 
 def test_printed_sizes_via_product():
-    for n, want in ((5, 109), (50, 10099)):
-        info = host(W.dfa_rn(n)).info()
-        assert info["n_sfa_states"] - 1 == want       # the all-sink map is a constant
-    assert host(W.dfa_even_odd(5)).info()["n_sfa_states"] - 1 == 21
+    """Every size printed in Sect. VI (tests/golden/sfa_sizes.txt), counted by
+    the product's construction.  r_500 and r_a have more than 256 states:
+    16-bit ids, with the point mappings counted but not stored."""
+    from conftest import read_golden
+    make = {"r_n": W.dfa_rn, "r_a": W.dfa_ra, "even_odd": W.dfa_even_odd}
+    for fam, n, D, Sd in ((r[0], int(r[1]), int(r[2]), int(r[3])) for r in read_golden("sfa_sizes.txt")):
+        d = make[fam](n)
+        info = host(d).info()
+        assert info["n_reachable"] - 1 == D             # the sink is not counted
+        assert info["n_sfa_states"] - 1 == Sd           # nor the all-sink mapping (a constant)
+        if info["n_reachable"] > 256:
+            assert info["id_bits"] == 16 and info["n_stored"] < 4 * info["n_reachable"]
+            assert info["placement"] == sfa.PLACE_SMEM_DFA_CLASSES | sfa.PLACE_GLOBAL_NC
+        else:
+            assert info["id_bits"] == 8 and info["n_stored"] == info["n_nonconst"]
+
+
+@pytest.mark.parametrize("n", [127, 128, 129, 300, 1000])
+def test_rn_sizes_across_the_id_width(n):
+    """k^2 + k - 1 non-constant D-SFA states for r_n (k = 2n; the closed
+    form the oracle pins on n <= 6), on both sides of 256 reachable states:
+    n = 127 stores every mapping, n >= 128 keeps the k^2 point mappings
+    implicit."""
+    k = 2 * n
+    info = host(W.dfa_rn(n)).info()
+    assert info["n_nonconst"] == k * k + k - 1
+    assert info["id_bits"] == (8 if n <= 127 else 16)
 
 
 def test_cap_switches_to_simulation():
@@ -189,7 +212,7 @@ def test_unreachable_states_are_trimmed():
 
 
 @pytest.mark.parametrize("case,code", [
-    ("nq0", sfa.ERR_INVALID), ("nq257", sfa.ERR_UNSUPPORTED), ("range", sfa.ERR_INVALID),
+    ("nq0", sfa.ERR_INVALID), ("nq4096", sfa.ERR_UNSUPPORTED), ("range", sfa.ERR_INVALID),
     ("q0", sfa.ERR_INVALID),
 ])
 def test_invalid_dfas(case, code):
@@ -200,9 +223,9 @@ def test_invalid_dfas(case, code):
     delta = np.zeros((4, 256), dtype=np.int32)
     if case == "nq0":
         nq = 0
-    elif case == "nq257":
-        nq = 257
-        delta = np.zeros((257, 256), dtype=np.int32)
+    elif case == "nq4096":
+        nq = 4096
+        delta = np.zeros((4096, 256), dtype=np.int32)
     elif case == "range":
         delta[2, 7] = 4
     elif case == "q0":

@@ -420,6 +420,12 @@ def workload_sim_automata(seed: int = SEED_SIM) -> List[DFA]:
     return [dfa_random(nq, 16, seed + nq) for nq in (16, 32, 64)]
 
 
+def workload_sim_automata_large(seed: int = SEED_SIM) -> List[DFA]:
+    """Random complete DFAs of 128 and 256 states over 16 symbols (the same
+    recipe as the simulation workload, past its 64 states)."""
+    return [dfa_random(nq, 16, seed + nq) for nq in (128, 256)]
+
+
 def workload_sim_text(n: int = 4 << 30, seed: int = SEED_SIM) -> np.ndarray:
     return text_uniform(n, bytes(range(16)), seed + 10)
 
