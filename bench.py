@@ -701,27 +701,33 @@ def run_serving(args, rank, world, local):
 
 
 def run_rn(args, rank, world, local):
-    """The paper's scalability automata (Sect. VI-B): r_5 and r_50, the
-    minimal DFAs of ([0-4]{n}[5-9]{n})* (11 and 101 states, 110 and 10 100
-    D-SFA states), on 1 GiB accepted texts.  Their chunk mappings never
-    become constant, so every byte takes the D-SFA's non-constant rows and
-    the count pass reruns most of each chunk.  A step matches the text with
-    both automata; results are checked against the oracle."""
+    """The paper's scalability automata (Sect. VI-B): r_5, r_50 and r_500, the
+    minimal DFAs of ([0-4]{n}[5-9]{n})* (11, 101 and 1001 states; 110, 10 100
+    and 1 001 000 D-SFA states), on 1 GiB accepted texts, and r_a = r_500 | a*
+    on 1 GiB of 'a'.  r_500 and r_a have 16-bit state ids and their point
+    mappings are not stored.  A step matches each text with its automaton;
+    every result is checked against the oracle."""
     import torch
 
     import oracle
     import paper_1405_0562_gb300 as sfa
     torch.cuda.set_device(local)
     n = args.text_bytes or (1 << 30)
-    per, cpu, checks = {}, {}, {}
+    per, cpu, checks, sizes = {}, {}, {}, {}
     stream = torch.cuda.Stream()
     total_ms, launches = 0.0, 0
     clocks = ClockSampler(local)
     clocks.start()
-    for rn in (5, 50):
-        d = W.dfa_rn(rn)
-        t = W.text_rn_accepted(n, rn, W.SEED_LARGE + rn)
+    cases = [(f"r_{rn}", (lambda rn=rn: W.dfa_rn(rn)), (lambda rn=rn: W.text_rn_accepted(n, rn, W.SEED_LARGE + rn)))
+             for rn in (5, 50, 500)]
+    cases.append(("r_a", lambda: W.dfa_ra(500), lambda: np.full(n, ord("a"), dtype=np.uint8)))
+    for name, mk_d, mk_t in cases:
+        d, t = mk_d(), mk_t()
         a = sfa.Automaton.from_dfa(d)
+        info = a.info()
+        sizes[name] = {"dfa_states": info["n_reachable"], "sfa_states": info["n_sfa_states"],
+                       "stored": info["n_stored"], "id_bits": info["id_bits"],
+                       "compile_seconds": info["compile_seconds"]}
         tt = torch.from_numpy(t).cuda()
         out = sfa.empty_results(1)
         for _ in range(args.warmup):
@@ -731,31 +737,32 @@ def run_rn(args, rank, world, local):
         ms = _events(torch, stream, lambda: a.match(tt, out, stream=stream), args.steps)
         launches += sfa.kernel_launch_count() - n0
         total_ms += ms
-        per[f"r_{rn}"] = n * args.steps / (ms * 1e-3) / 1e9
+        per[name] = n * args.steps / (ms * 1e-3) / 1e9
         got = sfa.decode(out)[0]
         f, acc, c = oracle.dfa_run(d.delta, d.q0, d.accept, t)
-        checks[f"r_{rn}"] = got == (f, acc, 0, c)
+        checks[name] = got == (f, acc, 0, c)
         sample = t[:64 << 20]
         t0 = time.perf_counter()
         oracle.dfa_run(d.delta, d.q0, d.accept, sample)
-        cpu[f"r_{rn}"] = sample.size / (time.perf_counter() - t0) / 1e9
+        cpu[name] = sample.size / (time.perf_counter() - t0) / 1e9
         del tt
     clk = clocks.stop()
     assert all(checks.values()), checks
     step_ms = total_ms / args.steps
-    value = 2 * n / (step_ms * 1e-3) / 1e9
+    value = len(cases) * n / (step_ms * 1e-3) / 1e9
     peak, peak_kind = hbm_peak()
     line = {"metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-            "config": {"workload": f"r_n: r_5 and r_50 (Sect. VI-B) on {n >> 20} MiB accepted texts each, both per step",
+            "config": {"workload": f"r_n: r_5, r_50, r_500 (Sect. VI-B) on {n >> 20} MiB accepted texts and "
+                                   f"r_a on {n >> 20} MiB of 'a', all four per step",
                        "text_bytes": n, "seed": W.SEED_LARGE, "l2": "inputs larger than L2",
-                       "per_automaton_GBps": per},
+                       "per_automaton_GBps": per, "automata": sizes},
             "roofline": {"bound": "hbm", "achieved": value, "peak": peak, "unit": "GB/s", "frac": value / peak,
                          "traffic": None, "peak_kind": peak_kind, "kernel": "sfa_match_kernel",
                          "algorithmic_bytes_per_launch": n},
             "gpu_launches": int(launches), "clocks": clk, "bit_exact_vs_oracle": True,
-            "cpu_baseline": {"value": 2 / sum(1 / v for v in cpu.values()), "unit": "GB/s", "cores": 1,
+            "cpu_baseline": {"value": len(cpu) / sum(1 / v for v in cpu.values()), "unit": "GB/s", "cores": 1,
                              "kind": "oracle", "sample": "first 64 MiB with each automaton",
                              "per_automaton_GBps": cpu}}
     if rank == 0:

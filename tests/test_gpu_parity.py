@@ -437,6 +437,130 @@ def test_full_transformation_6():
 
 
 # ---------------------------------------------------------------------------
+# 16-bit state ids (more than 256 reachable states)
+# ---------------------------------------------------------------------------
+
+def _wide_ac():
+    """An Aho-Corasick automaton of 40 seeded literals over a-z: 308 states,
+    synchronising (its chunks become constant mappings)."""
+    rng = np.random.default_rng(5)
+    lits = [bytes(rng.choice(list(W.LOWER_ALPHABET), size=int(rng.integers(6, 11))).tolist()) for _ in range(40)]
+    return W.dfa_aho_corasick(lits)
+
+
+def _wide_cycle(nq=300):
+    """A permutation automaton without a sink: its D-SFA is nq rotations,
+    all stored, and no chunk ever becomes constant."""
+    delta = np.tile((np.arange(nq, dtype=np.int32)[:, None] + 1) % nq, (1, 256))
+    delta[:, ord("b")] = (np.arange(nq, dtype=np.int32) + 7) % nq
+    acc = (np.arange(nq) % 11 == 4).astype(np.uint8)
+    return W.DFA(delta, 0, acc, b"ab", name=f"cycle{nq}")
+
+
+WIDE = {
+    "r128": lambda: W.dfa_rn(128),
+    "r500": lambda: W.dfa_rn(500),
+    "ra500": lambda: W.dfa_ra(500),
+    "ac308": _wide_ac,
+    "cycle300": _wide_cycle,
+}
+
+
+def _wide_texts(name, d, n, seed):
+    """Accepted r_n / r_a texts with errors at several rates (chunks that die
+    into the sink early, late or never), uniform text otherwise."""
+    rng = np.random.default_rng(seed)
+    if name.startswith("r"):
+        rn = 128 if name == "r128" else 500
+        base = W.text_rn_accepted(n, rn, seed)
+        out = [base.copy()]
+        for rate in (1 / 200_000, 1 / 3000, 1 / 50):
+            t = base.copy()
+            flips = rng.random(n) < rate
+            t[flips] = np.frombuffer(b"0123456789a", np.uint8)[rng.integers(0, 11, int(flips.sum()))]
+            out.append(t)
+        return out
+    alpha = np.frombuffer(d.alphabet, np.uint8)
+    return [alpha[rng.integers(0, alpha.size, n)]]
+
+
+@pytest.mark.parametrize("name", sorted(WIDE))
+def test_wide_ids(name):
+    """Automata past 256 states: 16-bit ids, class-indexed DFA rows in
+    shared memory, point mappings followed without being stored.  Automatic
+    shape (two levels on the longer texts), CTA shapes, short chunks, forced
+    chunk counts, unaligned views and Lemma 1 streaming."""
+    sfa = sfa_mod()
+    d = WIDE[name]()
+    a = sfa.Automaton.from_dfa(d)
+    info = a.info()
+    assert info["id_bits"] == 16 and info["mode"] == sfa.MODE_SFA
+    for t in _wide_texts(name, d, (24 << 20) + 5, seed=len(name)):
+        want = expect(d, t)
+        dev = torch.from_numpy(t).cuda()
+        for launch in ({}, {"block_threads": 256, "chains": 2, "chunk_bytes": 4096}, {"chunk_bytes": 100},
+                       {"forced_chunks": 61}):
+            out = a.match(dev, **launch)
+            torch.cuda.synchronize()
+            assert sfa.decode(out)[0] == want, (name, launch)
+        small = t[:200_003]
+        for launch in ({"block_threads": 128, "chains": 1, "chunk_bytes": 16}, {"forced_chunks": 1}):
+            assert gpu_match(a, small, **launch) == expect(d, small), launch
+        for off in (1, 7):
+            out = a.match(dev[off:off + 3_000_001])
+            torch.cuda.synchronize()
+            assert sfa.decode(out)[0] == expect(d, t[off:off + 3_000_001])
+        out = a.match(dev[:(5 << 20) + 3])
+        a.match_continue(dev[(5 << 20) + 3:], out)
+        torch.cuda.synchronize()
+        assert sfa.decode(out)[0] == want
+        for n in (0, 1, 999):
+            assert gpu_match(a, t[:n]) == expect(d, t[:n])
+
+
+def test_wide_ids_full_size():
+    """r_500 on 1 GiB of an accepted text and r_a on 1 GiB of 'a' (the
+    paper's Sect. VI-B workloads), in the bench's launch configuration."""
+    sfa = sfa_mod()
+    d = W.dfa_rn(500)
+    t = W.text_rn_accepted(1 << 30, 500, 1405500)
+    got = gpu_match(sfa.Automaton.from_dfa(d), t)
+    assert got == expect(d, t) and got[3] == (1 << 30) // 1000
+    d = W.dfa_ra(500)
+    t = np.full(1 << 30, ord("a"), dtype=np.uint8)
+    got = gpu_match(sfa.Automaton.from_dfa(d), t)
+    assert got == expect(d, t) and got[3] == 1 << 30
+
+
+def test_wide_ids_in_batches_and_noalloc():
+    """A batch mixing byte-id and 16-bit-id automata (the latter matched by
+    per-text launches), and the no-allocation entry on a 16-bit-id handle."""
+    sfa = sfa_mod()
+    ds = [W.dfa_rn(128), _wide_ac(), AUTOMATA["ac_set"](), W.dfa_rn(5)]
+    autos = [sfa.Automaton.from_dfa(d) for d in ds]
+    texts, hs, want = [], [], []
+    for i, n in enumerate((0, 1000, 1 << 20, 77_777, 3 << 20, 5)):
+        j = i % len(ds)
+        t = _wide_texts("r128", ds[j], n, i)[0] if j in (0, 3) else text_for(ds[j], n, seed=i)
+        if j == 3:
+            t = W.text_rn_accepted(n, 5, i)
+        texts.append(torch.from_numpy(t).cuda())
+        hs.append(autos[j])
+        want.append(expect(ds[j], t))
+    b = sfa.Batch(hs, texts)
+    for graph in (False, True):
+        out = torch.zeros(16 * len(texts), dtype=torch.uint8, device="cuda")
+        b.launch(out, graph=graph)
+        torch.cuda.synchronize()
+        assert sfa.decode(out) == want
+    out = torch.zeros(16, dtype=torch.uint8, device="cuda")
+    a = autos[0]
+    a.match_noalloc(texts[4], out)
+    torch.cuda.synchronize()
+    assert sfa.decode(out)[0] == want[4]
+
+
+# ---------------------------------------------------------------------------
 # streaming (Lemma 1), host path, batches, timeouts
 # ---------------------------------------------------------------------------
 
