@@ -308,10 +308,13 @@ def run_gpu(args, rank: int, world: int, local: int):
     # sustained: the same match back to back for about SUSTAIN_S seconds,
     # with the clock sampler still running, so that the clock record covers
     # a window of the same work (the timed region above lasts milliseconds)
-    sustained = sustained_run(torch, stream, lambda: a.match(text, out, stream=stream, **launch), t.size,
-                              step_hint_s=max(1e-5, 1e-3 * t_start.elapsed_time(t_end) / max(1, args.steps)))
+    sustained = None
+    if not args.profile:
+        sustained = sustained_run(torch, stream, lambda: a.match(text, out, stream=stream, **launch), t.size,
+                                  step_hint_s=max(1e-5, 1e-3 * t_start.elapsed_time(t_end) / max(1, args.steps)))
     clk = clocks.stop()
-    sustained["sm_mhz_median"] = clk["sm_mhz"]
+    if sustained:
+        sustained["sm_mhz_median"] = clk["sm_mhz"]
     total_ms = t_start.elapsed_time(t_end)
     kern_ms = [s.elapsed_time(e) for s, e in evs]
     total_ms = barrier_max(total_ms, world)
@@ -321,16 +324,18 @@ def run_gpu(args, rank: int, world: int, local: int):
     value = t.size * world / (step_ms * 1e-3) / 1e9
 
     # end to end through the host-buffer entry point (copies inside)
-    pinned = torch.from_numpy(t).pin_memory()
-    e2e_steps = max(1, min(args.steps, 5))
-    a.match_host(pinned, stream=stream)
-    torch.cuda.synchronize()
-    barrier(world)
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        res_h = a.match_host(pinned, stream=stream)
-    e2e_s = barrier_max((time.perf_counter() - t0) / e2e_steps, world)
-    assert res_h == got, (res_h, got)
+    e2e_s = None
+    if not args.profile:
+        pinned = torch.from_numpy(t).pin_memory()
+        e2e_steps = max(1, min(args.steps, 5))
+        a.match_host(pinned, stream=stream)
+        torch.cuda.synchronize()
+        barrier(world)
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            res_h = a.match_host(pinned, stream=stream)
+        e2e_s = barrier_max((time.perf_counter() - t0) / e2e_steps, world)
+        assert res_h == got, (res_h, got)
 
     peak, peak_kind = hbm_peak()
     kern_avg = statistics.mean(kern_ms)
@@ -338,13 +343,16 @@ def run_gpu(args, rank: int, world: int, local: int):
     traffic = profiled_traffic(args.workload)
     # the same text with the state ids a caller without a sample gets (the
     # uniform bank-conflict model)
-    a_uni = sfa.Automaton.from_dfa(d)
-    out_u = sfa.empty_results(1, text.device)
-    for _ in range(args.warmup):
-        a_uni.match(text, out_u, stream=stream, **launch)
-    uni_ms = _events(torch, stream, lambda: a_uni.match(text, out_u, stream=stream, **launch), args.steps) / args.steps
-    assert sfa.decode(out_u)[0] == got
-    read_peak = read_only_peak(torch, text.device)
+    uni_ms, read_peak = None, None
+    if not args.profile:
+        a_uni = sfa.Automaton.from_dfa(d)
+        out_u = sfa.empty_results(1, text.device)
+        for _ in range(args.warmup):
+            a_uni.match(text, out_u, stream=stream, **launch)
+        uni_ms = _events(torch, stream, lambda: a_uni.match(text, out_u, stream=stream, **launch),
+                         args.steps) / args.steps
+        assert sfa.decode(out_u)[0] == got
+        read_peak = read_only_peak(torch, text.device)
     line = {"metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u8", "data": "synthetic", "config": cfg,
@@ -352,14 +360,16 @@ def run_gpu(args, rank: int, world: int, local: int):
                          "frac": achieved / peak, "traffic": traffic,
                          "peak_kind": peak_kind, "kernel": "sfa_match_kernel",
                          "algorithmic_bytes_per_launch": int(t.size),
-                         "read_only_peak": read_peak, "frac_of_read_only_peak": achieved / read_peak["value"]},
-            "e2e": {"value": t.size * world / e2e_s / 1e9, "unit": "GB/s", "h2d_bytes_per_step": int(t.size),
-                    "d2h_bytes_per_step": 16},
+                         "read_only_peak": read_peak,
+                         "frac_of_read_only_peak": achieved / read_peak["value"] if read_peak else None},
+            "e2e": ({"value": t.size * world / e2e_s / 1e9, "unit": "GB/s", "h2d_bytes_per_step": int(t.size),
+                     "d2h_bytes_per_step": 16} if e2e_s else None),
             "gpu_launches": int(launches), "clocks": clk, "sustained": sustained,
-            "uniform_numbering": {"value": t.size / (uni_ms * 1e-3) / 1e9, "unit": "GB/s",
-                                  "frac": t.size / (uni_ms * 1e-3) / 1e9 / peak,
-                                  "note": "state ids from the uniform bank-conflict model (no text sample)"}}
-    if rank == 0 and not args.no_cpu_baseline:
+            "uniform_numbering": ({"value": t.size / (uni_ms * 1e-3) / 1e9, "unit": "GB/s",
+                                   "frac": t.size / (uni_ms * 1e-3) / 1e9 / peak,
+                                   "note": "state ids from the uniform bank-conflict model (no text sample)"}
+                                  if uni_ms else None)}
+    if rank == 0 and not args.no_cpu_baseline and not args.profile:
         base, res = cpu_baseline(d, t)
         line["cpu_baseline"] = base
         line["bit_exact_vs_oracle"] = (got == (res[0], res[1], 0, res[2]))
@@ -367,7 +377,7 @@ def run_gpu(args, rank: int, world: int, local: int):
             a.match(text[:CPU_PARALLEL_SAMPLE], out, stream=stream, **launch)
         stream.synchronize()
         line["cpu_parallel"] = cpu_parallel(d, t, sfa.decode(out)[0][0])
-    if args.workload == "plain_large" and not args.no_side_legs:
+    if args.workload == "plain_large" and not args.no_side_legs and not args.profile:
         # short legs of the other configurations, each checked against the
         # oracle, so that one default run covers them too
         del text
@@ -529,7 +539,13 @@ def run_batched(args, rank, world, local):
     views = [dev[offs[i]:offs[i + 1]] for i in range(len(lens))]
     hs = [autos[p] for p in pair]
     stream = torch.cuda.Stream()
-    b = sfa.Batch(hs, views)
+    # the plan's shape from the batch autotuner (cached per device, automaton
+    # mix and length histogram; tuning runs before the timed region)
+    from paper_1405_0562_gb300 import autotune
+    t_tune = time.perf_counter()
+    shape = autotune.tune_batch(hs, views)
+    t_tune = time.perf_counter() - t_tune
+    b = sfa.Batch(hs, views, **shape)
     out = sfa.empty_results(len(views))
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
@@ -558,7 +574,8 @@ def run_batched(args, rank, world, local):
         assert got[i] == (f, a, 0, c), i
     cfg = {"workload": "batched: 4096 texts log-uniform 256 B..16 MiB, uniform a-z, 8 literal-set automata "
                        "(51..159 states), one persistent launch under a CUDA graph",
-           "texts": len(views), "text_bytes": total, "seed": W.SEED_BATCH, "l2": "inputs larger than L2"}
+           "texts": len(views), "text_bytes": total, "seed": W.SEED_BATCH, "l2": "inputs larger than L2",
+           "plan_shape": shape or "automatic", "tuning_seconds": t_tune}
     value = total * world / (step_ms * 1e-3) / 1e9
     extra = {"plain_launches": {"value": total / (pms * 1e-3) / 1e9, "unit": "GB/s", "launches_per_step": len(views),
                                 "ms_per_step": pms},
@@ -647,8 +664,10 @@ def run_serving(args, rank, world, local):
     """Config 5: Poisson arrivals of requests (log-normal lengths, median
     64 KiB, sigma 1.5, cap 64 MiB, a-z) against 32 resident automata;
     continuous batching vs one request at a time, at offered loads of 0.5,
-    0.8 and 0.95 of the one-at-a-time capacity, and past it (2, 5, 10, 20
-    and 50 times), where requests queue up for the one-at-a-time loop."""
+    0.8 and 0.95 of the one-at-a-time capacity, and past it (2 to 200
+    times), where requests queue up for the one-at-a-time loop and the
+    server saturates the host link (texts copied in by one kernel per
+    batch from pinned memory)."""
     import torch
 
     import paper_1405_0562_gb300 as sfa
@@ -675,7 +694,7 @@ def run_serving(args, rank, world, local):
     by_id = {r.rid: r.result for r in alone}
     levels = {}
     best = 0.0
-    for load in (0.5, 0.8, 0.95, 2.0, 5.0, 10.0, 20.0, 50.0):
+    for load in (0.5, 0.8, 0.95, 2.0, 5.0, 10.0, 20.0, 50.0, 100.0, 200.0):
         rate = load * cap / mean
         arr, _, _ = W.workload_serving_requests(nreq, rate)
         srv = serve.Server(autos, hbm_budget=4 << 30, max_batch=256, slots=3)
@@ -853,6 +872,8 @@ def main():
     ap.add_argument("--check", action="store_true", help="sim: compare the full outputs with the oracle")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-side-legs", action="store_true", help="plain_large: skip the batched and sim legs")
+    ap.add_argument("--profile", action="store_true",
+                    help="only the timed matches (for ncu): no sustained loop, e2e, read peak, side or CPU legs")
     ap.add_argument("--text-bytes", type=int, default=0, help="override the text size (profiling runs only)")
     ap.add_argument("--chunk-bytes", type=int, default=0, help="launch shape override (default: automatic)")
     ap.add_argument("--block-threads", type=int, default=0, help="launch shape override (default: automatic)")

@@ -377,14 +377,18 @@ int sfa_batch_update(sfa_batch_t b, const sfa_handle_t *hs, const uint8_t *const
                      int32_t k, sfa_stream_t stream);
 
 /*
- * sfa_batch_update_host -- sfa_batch_update for texts still on the host: for
- * each i, enqueues one asynchronous copy of lens[i] bytes from h_texts[i]
- * (host; pinned, else the copy is synchronous) to d_dst[i] (device, the
- * caller's buffer) on `stream`, then replaces the work list by the k texts
- * at d_dst (as sfa_batch_update).  The serving loop's copy-in, with no
- * per-request runtime call from Python; the paper has no counterpart.
- * Errors as sfa_batch_update, plus CUDA when a copy cannot be enqueued
- * (copies enqueued before the failure stay enqueued).
+ * sfa_batch_update_host -- sfa_batch_update for texts still on the host: the
+ * lens[i] bytes at h_texts[i] are copied to d_dst[i] (device, the caller's
+ * buffer) on `stream`, then the work list is replaced by the k texts at
+ * d_dst (as sfa_batch_update).  Texts in host memory that the device can
+ * read (pinned memory mapped into its address space, as cudaHostAlloc and
+ * torch's pin_memory give; checked with cudaPointerGetAttributes) are copied
+ * by one kernel for the whole batch, at the host link's bandwidth, fastest
+ * when d_dst[i] and h_texts[i] have the same address modulo 16; other texts
+ * take one cudaMemcpyAsync each (synchronous for pageable memory).  The
+ * serving loop's copy-in; the paper has no counterpart.  Errors as
+ * sfa_batch_update, plus CUDA when a copy cannot be enqueued (copies
+ * enqueued before the failure stay enqueued).
  */
 int sfa_batch_update_host(sfa_batch_t b, const sfa_handle_t *hs, const uint8_t *const *h_texts,
                           uint8_t *const *d_dst, const uint64_t *lens, int32_t k, sfa_stream_t stream);
@@ -427,7 +431,31 @@ typedef struct {
     int32_t slots;            /* batches in flight, one stream each (0 = 3) */
     uint32_t chunk_bytes;     /* chunk length of the batch plans (0 = 1024) */
     uint32_t block_threads;   /* CTA size of the batch plans (0 = 512) */
+    uint32_t flags;           /* SFA_SERVER_* */
+    uint32_t reserved;
 } sfa_server_opts;
+
+#define SFA_SERVER_TIMING 1u  /* record device timestamps of every batch (sfa_server_spans) */
+
+/* The device timeline of one batch (SFA_SERVER_TIMING): CUDA-event times in
+ * ms since sfa_server_create, recorded on the batch's slot stream before the
+ * copy-in, between the copy-in and the match, and after the match.  An event
+ * is stamped when its stream reaches it, so a span also covers the time the
+ * batch's work waited for the device behind other slots' work. */
+typedef struct {
+    int32_t slot;             /* the batch slot (one stream each) */
+    int32_t requests;         /* requests in the batch */
+    uint64_t bytes;           /* text bytes of the batch */
+    float copy_start_ms;
+    float copy_end_ms;        /* = start of the match */
+    float match_end_ms;
+    float reserved;
+} sfa_batch_span;
+
+/* sfa_server_spans -- the spans of finished batches not returned yet, up to
+ * cap of them in out[] (*n of them), oldest first; 0 spans without
+ * SFA_SERVER_TIMING. */
+int sfa_server_spans(sfa_server_t s, sfa_batch_span *out, int32_t cap, int32_t *n);
 
 typedef struct {
     uint64_t tag;             /* the caller's tag of the request */
@@ -454,7 +482,8 @@ int sfa_server_create(const sfa_handle_t *automata, int32_t n, const sfa_server_
  * text of len bytes (pinned for asynchronous copies; it must stay valid and
  * unmodified until the request completes), and a tag returned with its
  * result.  INVALID for a bad index, a NULL text with len > 0, or a text
- * longer than the arena. */
+ * longer than the arena less 15 bytes (a text is placed at its host
+ * address's offset modulo 16 in its arena range). */
 int sfa_server_submit(sfa_server_t s, int32_t automaton, const uint8_t *h_text, uint64_t len, uint64_t tag);
 
 /* sfa_server_submit_many -- k requests at once (arrays of automaton indices,
@@ -486,6 +515,64 @@ int sfa_arena_alloc(sfa_arena_t a, uint64_t n, uint64_t *off);
 int sfa_arena_release(sfa_arena_t a, uint64_t off, uint64_t n);
 uint64_t sfa_arena_used(sfa_arena_t a);
 void sfa_arena_destroy(sfa_arena_t a);
+
+/* ---- regular expressions (the front end of Sect. VI) --------------------- */
+/*
+ * The pipeline of the paper's matcher (Sect. VI): a regular expression to
+ * an NFA by McNaughton and Yamada's position construction, to a DFA by the
+ * subset construction (Alg. 1), minimised (partition refinement), then the
+ * D-SFA by sfa_compile.  Host only.  Syntax (bytes): literals; escapes \n \t
+ * \r \f \v \0 \xHH and \ before a non-alphanumeric byte; \d \D \w \W \s \S;
+ * '.' (every byte but newline, every byte with SFA_REGEX_DOTALL); classes
+ * [...] with ranges and [^...]; groups (...) and (?:...); |; * + ? {m} {m,}
+ * {m,n} (m, n <= 1000).  No anchors, back-references or lazy quantifiers.
+ * The language is matched against whole prefixes of a text (a position is
+ * counted when the prefix ending there is in the language); with
+ * SFA_REGEX_SEARCH the automaton is that of (any byte)* r, so a position is
+ * counted when an occurrence of r ends there.
+ */
+#define SFA_REGEX_SEARCH      1u
+#define SFA_REGEX_DOTALL      2u
+#define SFA_REGEX_NO_MINIMIZE 4u   /* keep the subset automaton as built */
+
+typedef struct {
+    int32_t nq;               /* DFA states (the empty set of NFA states, a dead
+                                 state, included when reachable) */
+    int32_t q0;               /* initial state (0) */
+    int32_t positions;        /* positions of the expression (NFA states - 1) */
+    int32_t subset_states;    /* states of the subset construction, before minimising */
+    int32_t ncls;             /* byte classes of the expression */
+    int32_t reserved;
+} sfa_regex_info;
+
+/*
+ * sfa_regex_dfa -- the (minimal) DFA of a regular expression.
+ *   pattern, len  the expression's bytes (no terminator needed)
+ *   cap           capacity of delta/accept in states
+ *   delta         host int32[cap * 256] or NULL: written row-major as for
+ *                 sfa_compile, states numbered breadth first from q0 = 0
+ *   accept        host uint8[cap] or NULL (both or neither)
+ *   info          host, optional: sizes (filled also when the DFA does not fit)
+ *   err_pos       host, optional: byte offset of a syntax error
+ * Errors: INVALID (syntax, with *err_pos), UNSUPPORTED (more than cap states,
+ * or 4096 positions after {m,n} are expanded), OOM.
+ */
+int sfa_regex_dfa(const char *pattern, size_t len, uint32_t flags, int32_t cap, int32_t *delta, uint8_t *accept,
+                  sfa_regex_info *info, size_t *err_pos);
+
+/* sfa_regex_compile -- sfa_regex_dfa then sfa_compile (up to 4095 DFA states). */
+int sfa_regex_compile(const char *pattern, size_t len, uint32_t flags, const sfa_compile_opts *opts,
+                      sfa_handle_t *out);
+
+/*
+ * sfa_regex_nsfa_states -- the size of the N-SFA of the expression's
+ * position NFA (Definition 1 over correspondences, built by Alg. 4: f_I(q) =
+ * {q}, f_next(q) = the union of delta(q', sigma) over q' in f(q)); Theorem 2
+ * bounds it by 2^(n^2) for n NFA states.  The matcher runs D-SFAs; this
+ * reports what the nondeterministic construction would cost.  UNSUPPORTED
+ * (with *n_states = cap) past cap states.
+ */
+int sfa_regex_nsfa_states(const char *pattern, size_t len, uint32_t flags, uint64_t cap, uint64_t *n_states);
 
 /* ---- launch statistics (for benchmarks) --------------------------------- */
 /* Number of kernels the library enqueued since load (all entry points). */

@@ -32,6 +32,8 @@ DEBUG_SKIP_PUBLISH = 1
 TABLE_CLASS, TABLE_DFA, TABLE_NC, TABLE_MAPS, TABLE_ORIG, TABLE_CDFA16, TABLE_MAPS16 = 0, 1, 2, 3, 4, 5, 6
 PLACE_SMEM_DFA, PLACE_SMEM_DFA_CLASSES, PLACE_GLOBAL_NC, PLACE_SMEM_VECTORS = 1, 2, 4, 8
 TILING_AUTO, TILING_CTA, TILING_WARP = 0, 1, 2
+SERVER_TIMING = 1
+REGEX_SEARCH, REGEX_DOTALL, REGEX_NO_MINIMIZE = 1, 2, 4
 RESULT_BYTES = 16
 
 # every symbol include/sfa.h declares
@@ -41,8 +43,10 @@ EXPORTED = (
     "sfa_batch_create", "sfa_batch_launch", "sfa_batch_graph_launch", "sfa_batch_destroy",
     "sfa_match_batch", "sfa_kernel_launch_count", "sfa_match_noalloc",
     "sfa_batch_reserve", "sfa_batch_update", "sfa_batch_update_host",
-    "sfa_server_create", "sfa_server_submit", "sfa_server_submit_many", "sfa_server_progress", "sfa_server_stats", "sfa_server_destroy",
+    "sfa_server_create", "sfa_server_submit", "sfa_server_submit_many", "sfa_server_progress", "sfa_server_stats",
+    "sfa_server_spans", "sfa_server_destroy",
     "sfa_arena_create", "sfa_arena_alloc", "sfa_arena_release", "sfa_arena_used", "sfa_arena_destroy",
+    "sfa_regex_dfa", "sfa_regex_compile", "sfa_regex_nsfa_states",
 )
 
 
@@ -82,7 +86,19 @@ class Result(ctypes.Structure):
 
 class ServerOpts(ctypes.Structure):
     _fields_ = [("hbm_budget", ctypes.c_uint64), ("max_batch", ctypes.c_int32), ("slots", ctypes.c_int32),
-                ("chunk_bytes", ctypes.c_uint32), ("block_threads", ctypes.c_uint32)]
+                ("chunk_bytes", ctypes.c_uint32), ("block_threads", ctypes.c_uint32),
+                ("flags", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+
+
+class BatchSpan(ctypes.Structure):
+    _fields_ = [("slot", ctypes.c_int32), ("requests", ctypes.c_int32), ("bytes", ctypes.c_uint64),
+                ("copy_start_ms", ctypes.c_float), ("copy_end_ms", ctypes.c_float),
+                ("match_end_ms", ctypes.c_float), ("reserved", ctypes.c_float)]
+
+
+class RegexInfo(ctypes.Structure):
+    _fields_ = [("nq", ctypes.c_int32), ("q0", ctypes.c_int32), ("positions", ctypes.c_int32),
+                ("subset_states", ctypes.c_int32), ("ncls", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class Completion(ctypes.Structure):
@@ -137,6 +153,7 @@ def lib():
     L.sfa_server_submit_many.argtypes = [P, i32, P, P, P, P]
     L.sfa_server_progress.argtypes = [P, ctypes.POINTER(Completion), i32, ctypes.POINTER(i32)]
     L.sfa_server_stats.argtypes = [P, ctypes.POINTER(ServerStats)]
+    L.sfa_server_spans.argtypes = [P, ctypes.POINTER(BatchSpan), i32, ctypes.POINTER(i32)]
     L.sfa_server_destroy.argtypes = [P]
     L.sfa_server_destroy.restype = None
     L.sfa_arena_create.argtypes = [u64]
@@ -146,6 +163,10 @@ def lib():
     L.sfa_arena_used.argtypes = [P]
     L.sfa_arena_used.restype = u64
     L.sfa_arena_destroy.argtypes = [P]
+    L.sfa_regex_dfa.argtypes = [ctypes.c_char_p, ctypes.c_size_t, u32, i32, P, P, ctypes.POINTER(RegexInfo),
+                                ctypes.POINTER(ctypes.c_size_t)]
+    L.sfa_regex_compile.argtypes = [ctypes.c_char_p, ctypes.c_size_t, u32, P, ctypes.POINTER(P)]
+    L.sfa_regex_nsfa_states.argtypes = [ctypes.c_char_p, ctypes.c_size_t, u32, u64, ctypes.POINTER(u64)]
     L.sfa_arena_destroy.restype = None
     for name in EXPORTED:
         if name not in ("sfa_destroy", "sfa_batch_destroy", "sfa_strerror", "sfa_kernel_launch_count",
@@ -228,6 +249,12 @@ class Automaton:
     @classmethod
     def from_dfa(cls, dfa, **kw):
         return cls(dfa.delta, dfa.q0, dfa.accept, **kw)
+
+    @classmethod
+    def from_regex(cls, pattern: bytes, search: bool = False, dotall: bool = False, **kw):
+        """The D-SFA of a regular expression's minimal DFA (sfa_regex_dfa)."""
+        delta, q0, acc, _ = regex_dfa(pattern, search=search, dotall=dotall)
+        return cls(delta, q0, acc, **kw)
 
     @property
     def handle(self):
@@ -369,6 +396,36 @@ def match_batch(automata: Sequence[Automaton], texts: Sequence, out=None, stream
     lens = (ctypes.c_uint64 * max(k, 1))(*[t.numel() for t in texts])
     _check(lib().sfa_match_batch(hs, ptrs, lens, k, _dev_ptr(out, "out"), _stream_ptr(stream)), "sfa_match_batch")
     return out
+
+
+def regex_dfa(pattern: bytes, search: bool = False, dotall: bool = False, minimize: bool = True):
+    """The DFA of a regular expression (sfa_regex_dfa): (delta int32 [nq, 256],
+    q0, accept uint8 [nq], info dict)."""
+    flags = (REGEX_SEARCH if search else 0) | (REGEX_DOTALL if dotall else 0) | (0 if minimize else REGEX_NO_MINIMIZE)
+    pat = bytes(pattern)
+    info, err = RegexInfo(), ctypes.c_size_t()
+    rc = lib().sfa_regex_dfa(pat, len(pat), flags, 1, None, None, ctypes.byref(info), ctypes.byref(err))
+    if rc == ERR_INVALID:
+        raise SfaError(rc, f"sfa_regex_dfa: syntax error at byte {err.value} of {pat!r}")
+    _check(rc, "sfa_regex_dfa")
+    nq = info.nq
+    delta = np.zeros((nq, 256), dtype=np.int32)
+    acc = np.zeros(nq, dtype=np.uint8)
+    _check(lib().sfa_regex_dfa(pat, len(pat), flags, nq, delta.ctypes.data, acc.ctypes.data, ctypes.byref(info),
+                               ctypes.byref(err)), "sfa_regex_dfa")
+    return delta, int(info.q0), acc, {f: getattr(info, f) for f, _ in RegexInfo._fields_ if f != "reserved"}
+
+
+def regex_nsfa_states(pattern: bytes, search: bool = False, dotall: bool = False, cap: int = 1 << 20):
+    """States of the N-SFA of the expression's position NFA, or None past cap."""
+    flags = (REGEX_SEARCH if search else 0) | (REGEX_DOTALL if dotall else 0)
+    pat = bytes(pattern)
+    n = ctypes.c_uint64()
+    rc = lib().sfa_regex_nsfa_states(pat, len(pat), flags, cap, ctypes.byref(n))
+    if rc == ERR_UNSUPPORTED:
+        return None
+    _check(rc, "sfa_regex_nsfa_states")
+    return int(n.value)
 
 
 def kernel_launch_count() -> int:

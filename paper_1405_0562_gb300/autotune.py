@@ -1,10 +1,14 @@
-"""Autotuner for the launch shape of a match: block size, chunks per thread
-and chunk length, timed with CUDA events on the device, cached in a JSON
-file keyed by (device, automaton shape, text-size bucket).
+"""Autotuner for the launch shape of a match and of a batch plan: block
+size, chunks per thread and chunk length, timed with CUDA events on the
+device, cached in a JSON file keyed by (device, automaton shape, text-size
+bucket) for single texts and by (device, automaton mix, length histogram)
+for batches.
 
     from paper_1405_0562_gb300 import autotune
     shape = autotune.tune(automaton, text_cuda_u8)       # dict of launch options
     out = automaton.match(text_cuda_u8, **shape)
+    bshape = autotune.tune_batch(automata, texts)        # options of sfa_batch_create
+    out = Batch(automata, texts, **bshape).launch(graph=True)
 
 The cache file is ``$SFA_TUNE_CACHE`` or ``~/.cache/sfa_gb300_tune.json``.
 Results never depend on the shape (Theorem 3: any division of the text gives
@@ -18,7 +22,7 @@ import os
 import threading
 from typing import Dict, List, Optional
 
-from . import MODE_SIM, TILING_WARP, SfaError, empty_results
+from . import MODE_SIM, TILING_WARP, Batch, SfaError, empty_results
 
 _LOCK = threading.Lock()
 
@@ -136,3 +140,85 @@ def cached(automaton, n: int, device_name: Optional[str] = None) -> Optional[Dic
     dev = device_name or torch.cuda.get_device_name()
     ent = _load().get(key_for(automaton.info(), n, dev))
     return dict(ent["shape"]) if ent else None
+
+
+# ---------------------------------------------------------------------------
+# batch plans (one persistent launch over many texts)
+# ---------------------------------------------------------------------------
+
+BATCH_SHAPES = [(512, 1), (1024, 1), (256, 2), (256, 1)]
+BATCH_CHUNKS = [0, 512, 1024, 2048, 4096]   # 0: the plan's automatic chunk length
+
+
+def batch_key(infos: List[dict], lens: List[int], device_name: str) -> str:
+    """The automaton mix (states and classes of each distinct automaton,
+    sorted) and the length histogram (texts per power-of-4 length bucket, in
+    eighths of the batch), with the total size's bucket."""
+    mix = sorted({(i["mode"], i["n_reachable"], i["ncls"]) for i in infos})
+    hist: Dict[int, int] = {}
+    for n in lens:
+        b = 0 if n <= 0 else (max(n, 1).bit_length() + 1) // 2
+        hist[b] = hist.get(b, 0) + 1
+    k = max(len(lens), 1)
+    q = ",".join(f"{b}:{round(8 * c / k)}" for b, c in sorted(hist.items()) if round(8 * c / k))
+    return f"batch|{device_name}|{mix}|h{q}|n{bucket(sum(lens))}"
+
+
+def batch_candidates() -> List[Dict[str, int]]:
+    out = [{}]
+    for th, ch in BATCH_SHAPES:
+        for c in BATCH_CHUNKS:
+            if th == 512 and ch == 1 and c == 0:
+                continue   # the default plan, already first
+            out.append({"block_threads": th, "chains": ch, "chunk_bytes": c})
+    return out
+
+
+def tune_batch(automata, texts, reps: int = 3, force: bool = False, verbose: bool = False) -> Dict[str, int]:
+    """Best sfa_batch_create options for this batch (automata[i] matches
+    texts[i], CUDA uint8 tensors), timed as CUDA-graph launches; every
+    candidate must give the same results."""
+    import torch
+    infos = [a.info() for a in automata]
+    lens = [int(t.numel()) for t in texts]
+    dev = torch.cuda.get_device_name()
+    key = batch_key(infos, lens, dev)
+    with _LOCK:
+        cache = _load()
+        if not force and key in cache:
+            return dict(cache[key]["shape"])
+    out = empty_results(max(len(texts), 1))
+    best, best_ms, ref = None, float("inf"), None
+    for shape in batch_candidates():
+        try:
+            b = Batch(automata, texts, **shape)
+        except SfaError:
+            continue   # shape outside the automata's shared-memory budget
+        try:
+            for _ in range(2):
+                b.launch(out, graph=True)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                b.launch(out, graph=True)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+        finally:
+            b.close()
+        res = bytes(out.cpu().numpy())
+        if ref is None:
+            ref = res
+        elif res != ref:
+            raise RuntimeError(f"batch shape {shape} changed the results")
+        if verbose:
+            print(f"  {shape} {sum(lens) / ms / 1e6:.1f} GB/s", flush=True)
+        if ms < best_ms:
+            best, best_ms = shape, ms
+    if best is None:
+        return {}
+    with _LOCK:
+        cache = _load()
+        cache[key] = {"shape": best, "ms": best_ms, "GBps": sum(lens) / best_ms / 1e6}
+        _store(cache)
+    return dict(best)

@@ -8,6 +8,7 @@
 #include <atomic>
 #include <cstddef>
 #include <cstdint>
+#include <vector>
 
 #include "host_compile.h"
 #include "launch.h"
@@ -121,6 +122,25 @@ int launch_kernel(const void *k, int threads, size_t smem, uint32_t ctas, int ma
                   const CUtensorMap *tmap_b, const sfa_dev::Tables *tabs,
                   const sfa_dev::TextDesc *descs, const uint32_t *tile_text, const sfa_dev::Scratch &S,
                   sfa_result *out);
+// Copy-in of host texts by one kernel (gather.cu): text i of a batch is
+// copied from src (a device address of host memory) to dst, len bytes.
+constexpr uint64_t GATHER_UNIT = 64 << 10;   // bytes per unit of work of the copy kernel
+struct GatherDesc {
+    const uint8_t *src;
+    uint8_t *dst;
+    uint64_t len;
+};
+// d_unit0[i] = first unit of text i, d_unit0[k] = all units (device arrays)
+int launch_gather(const GatherDesc *d_descs, const uint32_t *d_unit0, uint32_t k, uint32_t units, cudaStream_t s);
+// The device address of host memory the device can read (pinned and mapped
+// into the device's address space), or NULL.
+const uint8_t *device_readable(const uint8_t *h);
+
+// regex.cpp
+int regex_to_dfa(const char *pattern, size_t len, uint32_t flags, int32_t cap, std::vector<int32_t> &delta,
+                 std::vector<uint8_t> &accept, sfa_regex_info *info, size_t *err_pos);
+int regex_nsfa_states(const char *pattern, size_t len, uint32_t flags, uint64_t cap, uint64_t *n_states);
+
 // one text (sfa_match_ex / sfa_match_continue)
 int match_impl(sfa_handle *h, const uint8_t *d_text, uint64_t n, sfa_result *d_out, cudaStream_t s,
                const sfa_launch_opts *o, bool carry, int32_t *d_map = nullptr);

@@ -32,6 +32,7 @@ struct sfa_batch {
     uint64_t cap_tiles = 0;
     uint32_t nr_max = 0;
     size_t off_tabs = 0, off_descs = 0, off_maps = 0, off_tt = 0, mem_bytes = 0;
+    size_t off_gd = 0, off_gu = 0;      // copy-in by one kernel: descriptors, unit prefix sums
     uint8_t *d_mem = nullptr;
     uint8_t *d_scratch = nullptr;
     ScratchPlan plan{};
@@ -61,7 +62,9 @@ void set_layout(sfa_batch *b) {
     b->off_descs = align_up((size_t)b->cap_texts * sizeof(Tables), 256);
     b->off_maps = align_up(b->off_descs + (size_t)b->cap_texts * sizeof(TextDesc), 256);
     b->off_tt = align_up(b->off_maps + (size_t)b->cap_texts * sizeof(CUtensorMap), 256);
-    b->mem_bytes = align_up(b->off_tt + (size_t)(1 + 2 * b->cap_tiles) * 4, 256);
+    b->off_gd = align_up(b->off_tt + (size_t)(1 + 2 * b->cap_tiles) * 4, 256);
+    b->off_gu = b->off_gd + (size_t)b->cap_texts * sizeof(GatherDesc);
+    b->mem_bytes = align_up(b->off_gu + (size_t)(b->cap_texts + 1) * 4, 256);
 }
 
 // Chunk length of one text: `chunk`, shortened for texts that would not fill
@@ -347,16 +350,32 @@ int sfa_batch_reserve(int32_t max_texts, uint64_t max_tiles, uint32_t nr_max, co
     return SFA_OK;
 }
 
-int sfa_batch_update(sfa_batch_t b, const sfa_handle_t *hs, const uint8_t *const *d_texts, const uint64_t *lens,
-                     int32_t k, sfa_stream_t stream) {
+}  // extern "C"
+
+namespace {
+
+// sfa_batch_update, and (ng > 0) the copy-in of ng texts by one kernel:
+// gd[i] and gu[i] (first unit of text i; gu[ng] = all units) are staged with
+// the work list and the copy kernel runs before the work list upload
+int update_impl(sfa_batch_t b, const sfa_handle_t *hs, const uint8_t *const *d_texts, const uint64_t *lens,
+                int32_t k, cudaStream_t s, const GatherDesc *gd, const uint32_t *gu, uint32_t ng) {
     if (!b || !b->reserved) return SFA_ERR_INVALID;
-    if (k > b->cap_texts) return SFA_ERR_INVALID;
+    if (k > b->cap_texts || ng > (uint32_t)b->cap_texts) return SFA_ERR_INVALID;
     int rc = check_inputs(hs, d_texts, lens, k, b->device);
     if (rc) return rc;
-    cudaStream_t s = (cudaStream_t)stream;
     const int st = b->stage ^ 1;
     // the staging buffer may still be the source of the copy two updates ago
     CK(cudaEventSynchronize(b->ev_stage[st]));
+    if (ng) {
+        uint8_t *h = b->h_stage[st];
+        std::memcpy(h + b->off_gd, gd, (size_t)ng * sizeof(GatherDesc));
+        std::memcpy(h + b->off_gu, gu, (size_t)(ng + 1) * 4);
+        CK(cudaMemcpyAsync(b->d_mem + b->off_gd, h + b->off_gd, b->off_gu - b->off_gd + (size_t)(ng + 1) * 4,
+                           cudaMemcpyHostToDevice, s));
+        rc = launch_gather(reinterpret_cast<const GatherDesc *>(b->d_mem + b->off_gd),
+                           reinterpret_cast<const uint32_t *>(b->d_mem + b->off_gu), ng, gu[ng], s);
+        if (rc) return rc;
+    }
     const size_t prev_sims = b->sim_index.size();
     rc = fill_worklist(b, hs, d_texts, lens, k, b->h_stage[st]);
     if (rc) return rc;
@@ -380,6 +399,15 @@ int sfa_batch_update(sfa_batch_t b, const sfa_handle_t *hs, const uint8_t *const
     return SFA_OK;
 }
 
+}  // namespace
+
+extern "C" {
+
+int sfa_batch_update(sfa_batch_t b, const sfa_handle_t *hs, const uint8_t *const *d_texts, const uint64_t *lens,
+                     int32_t k, sfa_stream_t stream) {
+    return update_impl(b, hs, d_texts, lens, k, (cudaStream_t)stream, nullptr, nullptr, 0);
+}
+
 int sfa_batch_update_host(sfa_batch_t b, const sfa_handle_t *hs, const uint8_t *const *h_texts,
                           uint8_t *const *d_dst, const uint64_t *lens, int32_t k, sfa_stream_t stream) {
     if (!b || !b->reserved || k < 0 || k > b->cap_texts) return SFA_ERR_INVALID;
@@ -389,9 +417,26 @@ int sfa_batch_update_host(sfa_batch_t b, const sfa_handle_t *hs, const uint8_t *
     int rc = check_inputs(hs, reinterpret_cast<const uint8_t *const *>(d_dst), lens, k, b->device);
     if (rc) return rc;
     cudaStream_t s = (cudaStream_t)stream;
-    for (int32_t i = 0; i < k; ++i)
-        if (lens[i]) CK(cudaMemcpyAsync(d_dst[i], h_texts[i], lens[i], cudaMemcpyHostToDevice, s));
-    return sfa_batch_update(b, hs, reinterpret_cast<const uint8_t *const *>(d_dst), lens, k, stream);
+    // texts in host memory the device can read: one copy kernel for all;
+    // the others: one cudaMemcpyAsync each
+    std::vector<GatherDesc> gd;
+    std::vector<uint32_t> gu;
+    uint64_t units = 0;
+    for (int32_t i = 0; i < k; ++i) {
+        if (!lens[i]) continue;
+        const uint8_t *src = device_readable(h_texts[i]);
+        if (src) {
+            gu.push_back((uint32_t)units);
+            gd.push_back(GatherDesc{src, d_dst[i], lens[i]});
+            units += (lens[i] + GATHER_UNIT - 1) / GATHER_UNIT;
+        } else {
+            CK(cudaMemcpyAsync(d_dst[i], h_texts[i], lens[i], cudaMemcpyHostToDevice, s));
+        }
+    }
+    if (units >= (1ull << 32)) return SFA_ERR_INVALID;
+    gu.push_back((uint32_t)units);
+    return update_impl(b, hs, reinterpret_cast<const uint8_t *const *>(d_dst), lens, k, s, gd.data(), gu.data(),
+                       (uint32_t)gd.size());
 }
 
 int sfa_batch_launch(sfa_batch_t b, sfa_result *d_out, sfa_stream_t stream) {

@@ -19,6 +19,10 @@
 namespace {
 
 constexpr uint64_t ARENA_ALIGN = 256;
+// A request's text sits in its arena range at the same offset modulo 16 as
+// its host copy, so that the copy kernel moves 16-byte vectors on both sides;
+// ranges are TEXT_PAD bytes longer than their text for that.
+constexpr uint64_t TEXT_PAD = 15;
 
 uint64_t arena_round(uint64_t n) {
     return std::max<uint64_t>(ARENA_ALIGN, (n + ARENA_ALIGN - 1) / ARENA_ALIGN * ARENA_ALIGN);
@@ -85,6 +89,8 @@ struct Req {
 struct Slot {
     cudaStream_t stream = nullptr;
     cudaEvent_t ev = nullptr;
+    cudaEvent_t t_copy = nullptr, t_match = nullptr, t_end = nullptr;   // SFA_SERVER_TIMING
+    uint64_t bytes = 0;
     sfa_batch_t plan = nullptr;
     sfa_result *d_out = nullptr;
     sfa_result *h_out = nullptr;   // pinned
@@ -103,6 +109,9 @@ struct sfa_server {
     std::vector<Slot> slots;
     std::deque<Req> queue;
     std::deque<sfa_completion> done;
+    bool timing = false;
+    cudaEvent_t t_origin = nullptr;
+    std::deque<sfa_batch_span> spans;
     uint64_t batches = 0, requests = 0;
     std::vector<sfa_handle_t> hs;
     std::vector<const uint8_t *> src;
@@ -119,8 +128,11 @@ void server_free(sfa_server *s) {
         if (sl.d_out) cudaFree(sl.d_out);
         if (sl.h_out) cudaFreeHost(sl.h_out);
         if (sl.ev) cudaEventDestroy(sl.ev);
+        for (cudaEvent_t e : {sl.t_copy, sl.t_match, sl.t_end})
+            if (e) cudaEventDestroy(e);
         if (sl.stream) cudaStreamDestroy(sl.stream);
     }
+    if (s->t_origin) cudaEventDestroy(s->t_origin);
     if (s->d_arena) cudaFree(s->d_arena);
     delete s->arena;
     delete s;
@@ -133,9 +145,19 @@ int server_reap(sfa_server *s) {
         const cudaError_t q = cudaEventQuery(sl.ev);
         if (q == cudaErrorNotReady) continue;
         if (q != cudaSuccess) return sfa_impl::cuda_err(q);
+        if (s->timing) {
+            sfa_batch_span sp{};
+            sp.slot = (int32_t)(&sl - s->slots.data());
+            sp.requests = (int32_t)sl.reqs.size();
+            sp.bytes = sl.bytes;
+            cudaEventElapsedTime(&sp.copy_start_ms, s->t_origin, sl.t_copy);
+            cudaEventElapsedTime(&sp.copy_end_ms, s->t_origin, sl.t_match);
+            cudaEventElapsedTime(&sp.match_end_ms, s->t_origin, sl.t_end);
+            s->spans.push_back(sp);
+        }
         for (size_t i = 0; i < sl.reqs.size(); ++i) {
             s->done.push_back(sfa_completion{sl.reqs[i].tag, sl.h_out[i]});
-            if (sl.reqs[i].len) s->arena->release(sl.reqs[i].off, sl.reqs[i].len);
+            if (sl.reqs[i].len) s->arena->release(sl.reqs[i].off, sl.reqs[i].len + TEXT_PAD);
         }
         sl.reqs.clear();
         sl.busy = false;
@@ -151,7 +173,7 @@ int server_admit(sfa_server *s) {
         sl.reqs.clear();
         while (!s->queue.empty() && (int32_t)sl.reqs.size() < s->max_batch) {
             Req r = s->queue.front();
-            if (r.len && !s->arena->alloc(r.len, r.off)) break;
+            if (r.len && !s->arena->alloc(r.len + TEXT_PAD, r.off)) break;
             s->queue.pop_front();
             sl.reqs.push_back(r);
         }
@@ -165,12 +187,19 @@ int server_admit(sfa_server *s) {
             const Req &r = sl.reqs[i];
             s->hs[i] = s->automata[r.automaton];
             s->src[i] = r.text;
-            s->dst[i] = r.len ? s->d_arena + r.off : nullptr;
+            s->dst[i] = r.len ? s->d_arena + r.off + (reinterpret_cast<uintptr_t>(r.text) & 15u) : nullptr;
             s->lens[i] = r.len;
         }
-        int rc = sfa_batch_update_host(sl.plan, s->hs.data(), s->src.data(), s->dst.data(), s->lens.data(), k,
+        sl.bytes = 0;
+        for (int32_t i = 0; i < k; ++i) sl.bytes += s->lens[i];
+        int rc = SFA_OK;
+        if (s->timing) rc = sfa_impl::cuda_err(cudaEventRecord(sl.t_copy, sl.stream));
+        if (!rc)
+            rc = sfa_batch_update_host(sl.plan, s->hs.data(), s->src.data(), s->dst.data(), s->lens.data(), k,
                                        sl.stream);
+        if (!rc && s->timing) rc = sfa_impl::cuda_err(cudaEventRecord(sl.t_match, sl.stream));
         if (!rc) rc = sfa_batch_launch(sl.plan, sl.d_out, sl.stream);
+        if (!rc && s->timing) rc = sfa_impl::cuda_err(cudaEventRecord(sl.t_end, sl.stream));
         if (!rc) {
             cudaError_t e = cudaMemcpyAsync(sl.h_out, sl.d_out, (size_t)k * sizeof(sfa_result),
                                             cudaMemcpyDeviceToHost, sl.stream);
@@ -185,7 +214,7 @@ int server_admit(sfa_server *s) {
         if (rc) {
             // put the requests back at the head of the queue, in order
             for (int32_t i = k - 1; i >= 0; --i) {
-                if (sl.reqs[i].len) s->arena->release(sl.reqs[i].off, sl.reqs[i].len);
+                if (sl.reqs[i].len) s->arena->release(sl.reqs[i].off, sl.reqs[i].len + TEXT_PAD);
                 s->queue.push_front(sl.reqs[i]);
             }
             sl.reqs.clear();
@@ -229,6 +258,13 @@ int sfa_server_create(const sfa_handle_t *automata, int32_t n, const sfa_server_
     s->device = dev;
     s->automata.assign(automata, automata + n);
     s->max_batch = max_batch;
+    s->timing = (o.flags & SFA_SERVER_TIMING) != 0;
+    if (s->timing && (cudaEventCreate(&s->t_origin) != cudaSuccess || cudaEventRecord(s->t_origin, 0) != cudaSuccess ||
+                      cudaEventSynchronize(s->t_origin) != cudaSuccess)) {
+        cudaGetLastError();
+        server_free(s);
+        return SFA_ERR_CUDA;
+    }
     s->arena = new (std::nothrow) sfa_arena(budget);
     if (!s->arena || cudaMalloc(&s->d_arena, budget) != cudaSuccess) {
         cudaGetLastError();
@@ -247,6 +283,9 @@ int sfa_server_create(const sfa_handle_t *automata, int32_t n, const sfa_server_
         int rc = sfa_batch_reserve(max_batch, max_tiles, nr_max, &lo, &sl.plan);
         if (!rc && cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess) rc = SFA_ERR_CUDA;
         if (!rc && cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming) != cudaSuccess) rc = SFA_ERR_CUDA;
+        if (!rc && s->timing)
+            for (cudaEvent_t *e : {&sl.t_copy, &sl.t_match, &sl.t_end})
+                if (!rc && cudaEventCreate(e) != cudaSuccess) rc = SFA_ERR_CUDA;
         if (!rc && cudaMalloc(&sl.d_out, (size_t)max_batch * sizeof(sfa_result)) != cudaSuccess) rc = SFA_ERR_OOM;
         if (!rc && cudaMallocHost(&sl.h_out, (size_t)max_batch * sizeof(sfa_result)) != cudaSuccess)
             rc = SFA_ERR_OOM;
@@ -262,7 +301,7 @@ int sfa_server_create(const sfa_handle_t *automata, int32_t n, const sfa_server_
 
 int sfa_server_submit(sfa_server_t s, int32_t automaton, const uint8_t *h_text, uint64_t len, uint64_t tag) {
     if (!s || automaton < 0 || automaton >= (int32_t)s->automata.size()) return SFA_ERR_INVALID;
-    if ((len && !h_text) || len > s->arena->size) return SFA_ERR_INVALID;
+    if ((len && !h_text) || len + TEXT_PAD > s->arena->size) return SFA_ERR_INVALID;
     s->queue.push_back(Req{automaton, h_text, len, tag, 0});
     return SFA_OK;
 }
@@ -272,7 +311,7 @@ int sfa_server_submit_many(sfa_server_t s, int32_t k, const int32_t *automata, c
     if (!s || k < 0 || (k > 0 && (!automata || !h_texts || !lens || !tags))) return SFA_ERR_INVALID;
     for (int32_t i = 0; i < k; ++i) {   // all or nothing
         if (automata[i] < 0 || automata[i] >= (int32_t)s->automata.size()) return SFA_ERR_INVALID;
-        if ((lens[i] && !h_texts[i]) || lens[i] > s->arena->size) return SFA_ERR_INVALID;
+        if ((lens[i] && !h_texts[i]) || lens[i] + TEXT_PAD > s->arena->size) return SFA_ERR_INVALID;
     }
     for (int32_t i = 0; i < k; ++i) s->queue.push_back(Req{automata[i], h_texts[i], lens[i], tags[i], 0});
     return SFA_OK;
@@ -290,6 +329,17 @@ int sfa_server_progress(sfa_server_t s, sfa_completion *done, int32_t cap, int32
     }
     *n_done = k;
     return rc;
+}
+
+int sfa_server_spans(sfa_server_t s, sfa_batch_span *out, int32_t cap, int32_t *n) {
+    if (!s || !n || cap < 0 || (cap > 0 && !out)) return SFA_ERR_INVALID;
+    int32_t m = 0;
+    while (m < cap && !s->spans.empty()) {
+        out[m++] = s->spans.front();
+        s->spans.pop_front();
+    }
+    *n = m;
+    return SFA_OK;
 }
 
 int sfa_server_stats(sfa_server_t s, sfa_server_stats_t *out) {

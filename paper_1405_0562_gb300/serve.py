@@ -6,9 +6,10 @@ HBM text budget and the batch capacity allow, copies the admitted texts into
 a device arena and matches them in one persistent launch per batch.  The
 loop itself is native (``sfa_server_*`` in the C ABI): the queue, the arena
 allocator, the batch slots (each on its own CUDA stream, several in flight)
-and the completion polling by CUDA events run in C++, one cudaMemcpyAsync
-per request and one launch per batch, with no allocation and no host wait on
-the launch path.  This module drives it: it submits requests at their
+and the completion polling by CUDA events run in C++: texts in pinned host
+memory are copied in by one kernel per batch (other texts by one
+cudaMemcpyAsync each) and matched by one launch per batch, with no
+allocation and no host wait on the launch path.  This module drives it: it submits requests at their
 arrival times, collects completions and stamps each request's latency
 (completion time minus arrival time on the host clock).
 
@@ -24,7 +25,8 @@ from typing import Dict, List, Optional, Sequence
 
 import numpy as np
 
-from . import (Automaton, Completion, RESULT_BYTES, ServerOpts, ServerStats, _check, decode, lib)
+from . import (SERVER_TIMING, Automaton, BatchSpan, Completion, RESULT_BYTES, ServerOpts, ServerStats, _check,
+               decode, lib)
 
 _ALIGN = 256
 
@@ -92,13 +94,16 @@ class Server:
     (the native server, driven from Python)."""
 
     def __init__(self, automata: Sequence[Automaton], hbm_budget: int = 4 << 30, max_batch: int = 256,
-                 slots: int = 3, chunk_bytes: int = 1024, block_threads: int = 512, device=None):
+                 slots: int = 3, chunk_bytes: int = 1024, block_threads: int = 512, device=None,
+                 timing: bool = False):
+        """timing: record each batch's device timeline (spans())."""
         import torch
         if device is not None:
             torch.cuda.set_device(device)
         self.automata = list(automata)
         hs = (ctypes.c_void_p * len(self.automata))(*[a.handle.value for a in self.automata])
-        opts = ServerOpts(hbm_budget, max_batch, slots, chunk_bytes, block_threads)
+        opts = ServerOpts(hbm_budget, max_batch, slots, chunk_bytes, block_threads,
+                          SERVER_TIMING if timing else 0, 0)
         s = ctypes.c_void_p()
         _check(lib().sfa_server_create(hs, len(self.automata), ctypes.byref(opts), ctypes.byref(s)),
                "sfa_server_create")
@@ -150,6 +155,18 @@ class Server:
         st = ServerStats()
         _check(lib().sfa_server_stats(self._s, ctypes.byref(st)), "sfa_server_stats")
         return {f: int(getattr(st, f)) for f, _ in ServerStats._fields_}
+
+    def spans(self) -> List[dict]:
+        """Device timelines of the batches finished since the last call
+        (SFA_SERVER_TIMING): slot, requests, bytes, copy start / end and
+        match end in ms since the server was created."""
+        out, n, res = (BatchSpan * 256)(), ctypes.c_int32(), []
+        while True:
+            _check(lib().sfa_server_spans(self._s, out, 256, ctypes.byref(n)), "sfa_server_spans")
+            res += [{f: getattr(out[i], f) for f, _ in BatchSpan._fields_ if f != "reserved"}
+                    for i in range(n.value)]
+            if n.value < 256:
+                return res
 
     @property
     def batches(self) -> int:

@@ -167,3 +167,92 @@ def test_server_results_equal_alone(sfa):
     assert st["requests"] == len(done) and st["batches"] >= len(done) // 8
     for r in again:
         assert r.result == by_id[r.rid], r.rid
+
+
+def test_copy_in_kernel_and_copies(sfa):
+    """sfa_batch_update_host copies pinned texts with one kernel (same or
+    different address modulo 16 on both sides; lengths around the 16-byte
+    vectors and the 64 KiB units) and pageable texts with cudaMemcpyAsync:
+    the arena holds exactly the host bytes afterwards and every result
+    equals the oracle's."""
+    autos_d = W.workload_serving_automata(3)
+    autos = [sfa.Automaton.from_dfa(d) for d in autos_d]
+    nr_max = max(a.info()["n_reachable"] for a in autos)
+    L = sfa.lib()
+    opts = sfa.LaunchOpts(1024, 512, 1, 0, 0, 0, 0, 0)
+    plan = ctypes.c_void_p()
+    assert L.sfa_batch_reserve(64, 8192, nr_max, ctypes.byref(opts), ctypes.byref(plan)) == sfa.OK
+    stream = torch.cuda.Stream()
+    big = torch.from_numpy(W.text_uniform(16 << 20, W.LOWER_ALPHABET, 77)).pin_memory()
+    arena = torch.zeros(32 << 20, dtype=torch.uint8, device="cuda")
+    lens = [0, 1, 15, 16, 17, 100, 65535, 65536, 65537, 131072 + 3, 3 << 20, 5 << 20]
+    try:
+        for shift in (0, 1, 8, 15):
+            srcs, dsts, texts, keep = [], [], [], []
+            pos, dpos = 3, 256
+            for i, n in enumerate(lens):
+                if i % 3 == 2:
+                    t = W.text_uniform(n, W.LOWER_ALPHABET, 500 + i)     # pageable: one copy each
+                    keep.append(t)
+                    srcs.append(t.ctypes.data if n else 0)
+                    texts.append(t)
+                    off = 0
+                else:
+                    srcs.append(big.data_ptr() + pos)                    # pinned: the copy kernel
+                    texts.append(big[pos:pos + n].numpy())
+                    off = pos & 15
+                    pos += n + 7
+                d = dpos + (off + shift) % 16
+                dsts.append(arena.data_ptr() + d)
+                dpos = (d + n + 255) // 256 * 256
+            k = len(lens)
+            which = [i % len(autos) for i in range(k)]
+            hs = (ctypes.c_void_p * k)(*[autos[j].handle.value for j in which])
+            src = (ctypes.c_void_p * k)(*srcs)
+            dst = (ctypes.c_void_p * k)(*dsts)
+            ln = (ctypes.c_uint64 * k)(*lens)
+            out = torch.zeros(16 * 64, dtype=torch.uint8, device="cuda")
+            arena.zero_()
+            torch.cuda.synchronize()
+            assert L.sfa_batch_update_host(plan, hs, src, dst, ln, k, stream.cuda_stream) == sfa.OK
+            assert L.sfa_batch_launch(plan, out.data_ptr(), stream.cuda_stream) == sfa.OK
+            stream.synchronize()
+            host = arena.cpu().numpy()
+            for i, n in enumerate(lens):
+                o = dsts[i] - arena.data_ptr()
+                assert np.array_equal(host[o:o + n], texts[i]), (shift, i, n)
+            assert sfa.decode(out[:16 * k]) == [expect(autos_d[j], t) for j, t in zip(which, texts)], shift
+    finally:
+        L.sfa_batch_destroy(plan)
+
+
+def test_server_slots_overlap_and_spans(sfa):
+    """The server with device timing: every batch reports its span; batches
+    of different slots are in flight at the same time (their spans, from
+    CUDA events on the slots' streams, intersect); results equal the
+    oracle's.  Requests all arrive at once, from one pinned buffer."""
+    from paper_1405_0562_gb300 import serve
+    autos_d = W.workload_serving_automata(8)
+    autos = [sfa.Automaton.from_dfa(d) for d in autos_d]
+    _, lens, which = W.workload_serving_requests(1500, rate_per_s=1.0, n_automata=len(autos))
+    total = int(lens.sum())
+    host = torch.from_numpy(W.text_uniform(total, W.LOWER_ALPHABET, 31)).pin_memory()
+    offs = np.concatenate([[0], np.cumsum(lens)])
+    reqs = [serve.Request(i, int(which[i]), host[offs[i]:offs[i + 1]], 0.0) for i in range(len(lens))]
+    srv = serve.Server(autos, hbm_budget=1 << 30, max_batch=128, slots=3, timing=True)
+    try:
+        done = srv.run(reqs, realtime=False)
+        spans = srv.spans()
+        batches = srv.batches
+    finally:
+        srv.close()
+    assert len(done) == len(reqs)
+    assert len(spans) == batches and sum(s["requests"] for s in spans) == len(reqs)
+    assert sum(s["bytes"] for s in spans) == total
+    for s in spans:
+        assert s["copy_start_ms"] <= s["copy_end_ms"] <= s["match_end_ms"]
+    overlap = any(a["slot"] != b["slot"] and a["copy_start_ms"] < b["match_end_ms"] and
+                  b["copy_start_ms"] < a["match_end_ms"] for a in spans for b in spans)
+    assert overlap
+    for r in done[::17]:
+        assert r.result == expect(autos_d[r.automaton], r.text.numpy()), r.rid
