@@ -337,9 +337,10 @@ int sfa_match_noalloc(sfa_handle_t h, const uint8_t *d_text, uint64_t n, sfa_res
  * sfa_batch_create -- plans one persistent launch over k texts, each matched
  * with its own automaton (Theorem 3 applied per text: every text gets its own
  * look-back chain of tiles).
- *   hs       host, k handles (all compiled on the current device; handles
- *            in simulation mode or with 16-bit state ids are matched by
- *            per-text launches)
+ *   hs       host, k handles (all compiled on the current device).  The
+ *            texts of simulation-mode handles run in one more persistent
+ *            launch per vector size (16, 32, 64, 128 or 256 entries); texts
+ *            of handles with 16-bit state ids take per-text launches
  *   d_texts  host array of k device pointers
  *   lens     host, k lengths
  *   opts     launch shape (NULL = automatic)

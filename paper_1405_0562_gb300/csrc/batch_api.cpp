@@ -53,6 +53,13 @@ struct sfa_batch {
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t exec = nullptr;
     sfa_result *exec_out = nullptr;
+    // The texts a plan takes: 0 = D-SFA texts of byte-id automata; > 0 =
+    // simulation-mode texts whose vectors have this many entries.  An exact
+    // plan holds one sub-plan per vector size among its texts (each a
+    // persistent launch of that size's kernel); texts of 16-bit-id automata,
+    // and simulation texts of reserved plans, take per-text launches.
+    int want_simnq = 0;
+    std::vector<sfa_batch *> subs;
 };
 
 namespace {
@@ -112,7 +119,12 @@ int fill_worklist(sfa_batch *b, const sfa_handle_t *hs, const uint8_t *const *d_
     std::map<sfa_handle_t, uint32_t> tab_of;
     for (int32_t i = 0; i < k; ++i) {
         sfa_handle_t h = hs[i];
-        if (h->host.mode == SFA_MODE_SIM || h->host.wide) {
+        const bool sim = h->host.mode == SFA_MODE_SIM;
+        if (b->want_simnq > 0) {
+            if (!sim || simnq_for((uint32_t)h->host.nr) != b->want_simnq) continue;   // another plan's
+        } else if (sim && !b->reserved) {
+            continue;   // a sub-plan's
+        } else if (sim || h->host.wide) {
             b->sim_index.push_back(i);
             b->sim_handle.push_back(h);
             b->sim_text.push_back(d_texts[i]);
@@ -199,6 +211,10 @@ int size_sim_scratch(sfa_batch *b) {
 }
 
 int batch_enqueue(sfa_batch *b, sfa_result *d_out, cudaStream_t s) {
+    for (sfa_batch *sub : b->subs) {
+        int rc = batch_enqueue(sub, d_out, s);
+        if (rc) return rc;
+    }
     if (b->reserved || b->total_tiles > 0) {
         CK(cudaMemsetAsync(b->d_scratch, 0, b->plan.zero, s));
         // reserved plans launch every resident CTA: the tile count is read on
@@ -218,7 +234,19 @@ int batch_enqueue(sfa_batch *b, sfa_result *d_out, cudaStream_t s) {
     return SFA_OK;
 }
 
+// kernels one launch of the plan enqueues
+uint64_t batch_launches(const sfa_batch *b) {
+    uint64_t n = (b->reserved || b->total_tiles > 0 ? 1 : 0) + b->sim_index.size();
+    for (const sfa_batch *sub : b->subs) n += batch_launches(sub);
+    return n;
+}
+
 void batch_free(sfa_batch *b) {
+    for (sfa_batch *sub : b->subs) {
+        batch_free(sub);
+        delete sub;
+    }
+    b->subs.clear();
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
     if (b->d_mem) cudaFree(b->d_mem);
@@ -233,6 +261,15 @@ int init_shape(sfa_batch *b, const sfa_launch_opts *opts) {
     Shape &sh = b->shape;
     sh.threads = 512;   // two CTAs per SM for automata up to ~150 states
     sh.chains = 1;
+    if (b->want_simnq) {
+        // the single-text simulation shapes; the caller's options do not apply
+        sh.threads = b->want_simnq > 64 ? 256 : 128;
+        sh.simnq = b->want_simnq;
+        if (opts && opts->timeout_us) sh.timeout_us = opts->timeout_us;
+        if (opts) sh.debug = opts->debug_flags;
+        b->kernel = kernel_for(sh.threads, 1, b->want_simnq, true);
+        return b->kernel ? SFA_OK : SFA_ERR_UNSUPPORTED;
+    }
     if (opts) {
         if (opts->block_threads) sh.threads = (int)opts->block_threads;
         if (opts->chains) sh.chains = (int)opts->chains;
@@ -249,53 +286,58 @@ int init_shape(sfa_batch *b, const sfa_launch_opts *opts) {
 
 int alloc_device(sfa_batch *b) {
     set_layout(b);
-    b->plan = plan_scratch((uint32_t)std::max(b->cap_texts, 1), b->cap_tiles, std::max<uint32_t>(b->nr_max, 1), 0);
+    const uint32_t nrm = std::max<uint32_t>(b->nr_max, 1);
+    // simulation plans: a chunk vector of nr_max bytes per chunk
+    const uint64_t vec = b->want_simnq ? b->cap_tiles * (uint64_t)b->shape.threads * b->shape.chains * nrm : 0;
+    b->plan = plan_scratch((uint32_t)std::max(b->cap_texts, 1), b->cap_tiles, nrm, vec);
     CK(cudaMalloc(&b->d_mem, b->mem_bytes));
     CK(cudaMalloc(&b->d_scratch, b->plan.total));
-    b->S = make_scratch(b->d_scratch, b->plan, std::max<uint32_t>(b->nr_max, 1), 0, b->shape);
-    b->smem = smem_bytes(b->shape.threads, b->shape.chains, std::max<uint32_t>(b->nr_max, 1));
+    b->S = make_scratch(b->d_scratch, b->plan, nrm, 0, b->shape);
+    b->smem = smem_bytes(b->shape.threads, b->shape.chains, nrm, b->want_simnq);
     blocks_per_sm(b->kernel, b->shape.threads, b->smem);   // cached before any capture
     return SFA_OK;
 }
 
-}  // namespace
-
-extern "C" {
-
-int sfa_batch_create(const sfa_handle_t *hs, const uint8_t *const *d_texts, const uint64_t *lens, int32_t k,
-                     const sfa_launch_opts *opts, sfa_batch_t *out) {
-    if (!out) return SFA_ERR_INVALID;
-    *out = nullptr;
-    int dev = 0;
-    CK(cudaGetDevice(&dev));
-    int rc = check_inputs(hs, d_texts, lens, k, dev);
-    if (rc) return rc;
+// An exact plan over the texts of kind `simnq` (see sfa_batch::want_simnq).
+int create_plan(const sfa_handle_t *hs, const uint8_t *const *d_texts, const uint64_t *lens, int32_t k,
+                const sfa_launch_opts *opts, int dev, int simnq, sfa_batch **out) {
     sfa_batch *b = new (std::nothrow) sfa_batch();
     if (!b) return SFA_ERR_OOM;
     b->device = dev;
-    rc = init_shape(b, opts);
+    b->want_simnq = simnq;
+    int rc = init_shape(b, opts);
     if (rc) {
         delete b;
         return rc;
     }
+    auto mine = [&](int32_t i) {
+        const bool sim = hs[i]->host.mode == SFA_MODE_SIM;
+        return simnq ? sim && simnq_for((uint32_t)hs[i]->host.nr) == simnq : !sim && !hs[i]->host.wide;
+    };
     const uint64_t cpt = (uint64_t)b->shape.threads * b->shape.chains;
     uint64_t total_bytes = 0;
     for (int32_t i = 0; i < k; ++i) {
-        if (hs[i]->host.mode == SFA_MODE_SIM || hs[i]->host.wide) continue;
+        if (!mine(i)) continue;
         b->nr_max = std::max<uint32_t>(b->nr_max, (uint32_t)hs[i]->host.nr);
         total_bytes += lens[i];
     }
-    // chunk length: as for one text of the batch's total size
-    b->chunk = opts && opts->chunk_bytes ? opts->chunk_bytes : 0;
+    // chunk length: D-SFA texts as for one text of the batch's total size
+    // (six tiles per resident CTA); simulation texts with one tile per
+    // resident CTA and at least 4 KiB, as for a single text (every chunk
+    // pays the vector phase)
+    b->chunk = !simnq && opts && opts->chunk_bytes ? opts->chunk_bytes : 0;
     if (!b->chunk) {
-        const size_t smem = smem_bytes(b->shape.threads, b->shape.chains, std::max<uint32_t>(b->nr_max, 1));
+        const size_t smem = smem_bytes(b->shape.threads, b->shape.chains, std::max<uint32_t>(b->nr_max, 1), simnq);
         const int bps = blocks_per_sm(b->kernel, b->shape.threads, smem);
         const uint64_t ctas = (uint64_t)std::max(1, bps) * std::max(1, device_props(dev).sms);
-        b->chunk = std::min<uint64_t>(4096, std::max<uint64_t>(256, align_up(total_bytes / (ctas * 6 * cpt), 16)));
+        if (simnq)
+            b->chunk = std::min<uint64_t>(MAX_CHUNK, std::max<uint64_t>(4096, align_up(total_bytes / (ctas * cpt), 64)));
+        else
+            b->chunk = std::min<uint64_t>(4096, std::max<uint64_t>(256, align_up(total_bytes / (ctas * 6 * cpt), 16)));
     }
     uint64_t tiles = 0;
     for (int32_t i = 0; i < k; ++i)
-        if (hs[i]->host.mode != SFA_MODE_SIM && !hs[i]->host.wide) tiles += text_tiles(lens[i], b->chunk, cpt);
+        if (mine(i)) tiles += text_tiles(lens[i], b->chunk, cpt);
     if (tiles >= (1ull << 30)) {
         delete b;
         return SFA_ERR_INVALID;
@@ -313,6 +355,41 @@ int sfa_batch_create(const sfa_handle_t *hs, const uint8_t *const *d_texts, cons
     if (rc) {
         batch_free(b);
         delete b;
+        return rc;
+    }
+    *out = b;
+    return SFA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sfa_batch_create(const sfa_handle_t *hs, const uint8_t *const *d_texts, const uint64_t *lens, int32_t k,
+                     const sfa_launch_opts *opts, sfa_batch_t *out) {
+    if (!out) return SFA_ERR_INVALID;
+    *out = nullptr;
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    int rc = check_inputs(hs, d_texts, lens, k, dev);
+    if (rc) return rc;
+    sfa_batch *b = nullptr;
+    rc = create_plan(hs, d_texts, lens, k, opts, dev, 0, &b);
+    // one sub-plan per vector size of the simulation-mode texts
+    for (int nq : {16, 32, 64, 128, 256}) {
+        bool any = false;
+        for (int32_t i = 0; i < k && !any; ++i)
+            any = hs[i]->host.mode == SFA_MODE_SIM && simnq_for((uint32_t)hs[i]->host.nr) == nq;
+        if (rc || !any) continue;
+        sfa_batch *sub = nullptr;
+        rc = create_plan(hs, d_texts, lens, k, opts, dev, nq, &sub);
+        if (!rc) b->subs.push_back(sub);
+    }
+    if (rc) {
+        if (b) {
+            batch_free(b);
+            delete b;
+        }
         return rc;
     }
     *out = b;
@@ -470,7 +547,7 @@ int sfa_batch_graph_launch(sfa_batch_t b, sfa_result *d_out, sfa_stream_t stream
         b->exec_out = d_out;
     }
     CK(cudaGraphLaunch(b->exec, (cudaStream_t)stream));
-    g_launches.fetch_add((b->reserved || b->total_tiles > 0 ? 1 : 0) + b->sim_index.size(), std::memory_order_relaxed);
+    g_launches.fetch_add(batch_launches(b), std::memory_order_relaxed);
     return SFA_OK;
 }
 

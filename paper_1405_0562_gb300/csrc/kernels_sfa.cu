@@ -55,7 +55,7 @@ size_t smem_bytes_common(int threads, int chains, uint32_t nr_max) {
 const void *kernel_for(int threads, int chains, int simnq, bool batch, bool wt) {
     if (wt) return batch || chains != 1 ? nullptr : kernel_for_wt(threads, simnq);
     if (simnq == 0) return kernel_for_sfa(threads, chains, batch);
-    if (batch) return nullptr;
+    if (batch) return chains == 1 ? kernel_for_sim_batch(threads, simnq) : nullptr;
     return kernel_for_sim(threads, chains, simnq);
 }
 

@@ -17,6 +17,8 @@ const void *kernel_for(int threads, int chains, int simnq, bool batch, bool wt =
 const void *kernel_for_sfa(int threads, int chains, bool batch);
 const void *kernel_for_sim(int threads, int chains, int simnq);
 const void *kernel_for_sim_large(int threads, int chains, int simnq);
+const void *kernel_for_sim_batch(int threads, int simnq);
+const void *kernel_for_sim_batch_large(int threads, int simnq);
 const void *kernel_for_wt(int threads, int simnq);
 // 16-bit state ids (more than 256 kept states): single texts, CTA tiles
 const void *kernel_for_wide(int threads, int chains);

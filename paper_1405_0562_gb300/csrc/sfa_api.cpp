@@ -218,7 +218,7 @@ Scratch make_scratch(uint8_t *base, const ScratchPlan &p, uint32_t nr_max, uint3
     S.debug = sh.debug;
     S.total_tiles = tiles;
     S.map_mode = 0;
-    S.pad_ = 0;
+    S.single = 0;
     return S;
 }
 
@@ -467,9 +467,12 @@ int match_impl(sfa_handle *h, const uint8_t *d_text, uint64_t n, sfa_result *d_o
     ScratchPlan p = plan_scratch(1, tiles, nr * (h->host.wide ? 2u : 1u), vec);
     rc = ensure_scratch(h, p.total);
     if (rc) return rc;
-    CK(cudaMemsetAsync(h->d_scratch, 0, p.zero, s));
+    // a text of one CTA tile: its CTA clears what it reads, no memset
+    const bool single = tiles == 1 && !sh.wt;
+    if (!single) CK(cudaMemsetAsync(h->d_scratch, 0, p.zero, s));
     Scratch S = make_scratch(h->d_scratch, p, nr, (uint32_t)tiles, sh);
     S.map_mode = d_map ? 1u : 0u;
+    S.single = single ? 1u : 0u;
     const void *k = shape_kernel(h, sh);
     const size_t smem = shape_smem(h, sh);
     alignas(64) CUtensorMap map, map_b;

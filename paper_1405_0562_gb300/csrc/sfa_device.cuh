@@ -788,6 +788,12 @@ __global__ void __launch_bounds__(THREADS, (min_ctas_per_sm<THREADS, CH, SIMNQ, 
     // single texts take one tile per CTA with automatic chunks)
     constexpr bool DEFER = BATCH && !WT;
     if (tid == 0) s_misc->dfr_valid = 0;
+    if (!BATCH && S.single && tid == 0) {
+        // the only CTA of the launch: nothing else reads these before the
+        // barrier that follows the first grab
+        S.hdr->err = 0;
+        S.texts[0].err = 0;
+    }
     auto grab = [&]() -> uint32_t {
         if (!two_levels) return atomicAdd(&S.hdr->tile_ctr, 1u);
         const uint32_t na = desc.split_tile, all = S.total_tiles;
@@ -812,7 +818,7 @@ __global__ void __launch_bounds__(THREADS, (min_ctas_per_sm<THREADS, CH, SIMNQ, 
             gt = __shfl_sync(0xffffffffu, gt, 0);
         } else {
             if (tid == 0) {
-                s_misc->tile = grab();
+                s_misc->tile = !BATCH && S.single ? 0u : grab();
                 s_misc->gconst = 0;
             }
             __syncthreads();
@@ -859,10 +865,15 @@ __global__ void __launch_bounds__(THREADS, (min_ctas_per_sm<THREADS, CH, SIMNQ, 
         const CUtensorMap *tmap_p = lvb ? &tmap_b : (d.map ? reinterpret_cast<const CUtensorMap *>(d.map) : &tmap);
         if (BATCH && d.map && d.rows2d && lane == 0) tensormap_acquire(d.map);
         const uint8_t *mtab = SIMNQ ? S.chainvec : T.maps;
+        // simulation chunk vectors: nr_max bytes apart (one text: nr_max = nr;
+        // a batch mixes automata of different sizes)
+        const uint32_t vstride = BATCH ? nr_max : nr;
         // a chunk or group mapping applied to a state
         auto amap = [&](uint32_t f, uint32_t v) -> uint32_t {
             if constexpr (WIDE)
                 return apply_map(f, v, T.maps16, nr, T.sink);
+            else if constexpr (SIMNQ > 0 && BATCH)
+                return f < nr ? f : (uint32_t)mtab[(size_t)(f - nr) * vstride + v];
             else
                 return apply_map(f, v, mtab, nr);
         };
@@ -1188,7 +1199,7 @@ __global__ void __launch_bounds__(THREADS, (min_ctas_per_sm<THREADS, CH, SIMNQ, 
             if (SIMNQ && V[c].mode != SIM_CONST) {
                 // keep the vector for the scan: id nr + global chunk index
                 const uint64_t gk = WT ? (uint64_t)gt * 32 + lane : (uint64_t)gt * CPT + (uint64_t)c * THREADS + tid;
-                uint8_t *dst = S.chainvec + gk * nr;
+                uint8_t *dst = S.chainvec + gk * vstride;
 #pragma unroll 4
                 for (int i = 0; i < NQ / 4; ++i) {
                     const uint32_t x = sim_word<NQ>(V[c], i);

@@ -103,7 +103,10 @@ struct Scratch {
     uint32_t map_mode;         // 1: every tile leaves its aggregate as a
                                // |Q|-vector in agg (constant tiles too), for
                                // the slice mapping of sfa_match_map
-    uint32_t pad_;
+    uint32_t single;           // 1: one text of one tile on one CTA; the CTA
+                               // clears the error words itself and takes
+                               // tile 0 without the counter, so the launch
+                               // needs no zeroed scratch
 };
 
 // chunks of a one-level text (the empty text, and one shorter than its

@@ -686,6 +686,41 @@ def test_batch_mixed_and_graph():
         assert gpu_match(hs[i], texts[i]) == want[i]
 
 
+def test_batch_with_simulation_texts_in_persistent_launches():
+    """Simulation-mode texts of a batch run in persistent launches too: one
+    per vector size (16, 32, 64, 128, 256 entries) beside the D-SFA launch,
+    whatever the number of texts; every result equals the oracle's, by plain
+    launch and by CUDA graph."""
+    sfa = sfa_mod()
+    sims = [W.dfa_random(nq, 16, seed=50 + nq) for nq in (12, 30, 60, 100, 200)]
+    dsfa = W.workload_batch_automata(2)
+    autos_d = sims + dsfa
+    autos = [sfa.Automaton.from_dfa(d) for d in autos_d]
+    assert [a.info()["mode"] for a in autos] == [sfa.MODE_SIM] * 5 + [sfa.MODE_SFA] * 2
+    rng = np.random.default_rng(11)
+    lens = [0, 1, 15, 64, 1000, 4096, 70_001, 1 << 20, 3 << 20, 8 << 20]
+    texts, hs, want = [], [], []
+    for i in range(30):
+        j = i % len(autos)
+        n = lens[i % len(lens)]
+        d = autos_d[j]
+        t = text_for(d, n, seed=i) if j >= len(sims) else W.text_uniform(n, bytes(range(16)), 900 + i)
+        texts.append(torch.from_numpy(t).cuda())
+        hs.append(autos[j])
+        want.append(expect(d, t))
+    b = sfa.Batch(hs, texts)
+    for graph in (False, True, True):
+        out = torch.zeros(16 * len(texts), dtype=torch.uint8, device="cuda")
+        n0 = sfa.kernel_launch_count()
+        b.launch(out, graph=graph)
+        torch.cuda.synchronize()
+        assert sfa.decode(out) == want, graph
+        assert sfa.kernel_launch_count() - n0 == 6        # one D-SFA launch, five vector sizes
+    out = sfa.match_batch(hs, texts)
+    torch.cuda.synchronize()
+    assert sfa.decode(out) == want
+
+
 def test_timeout_status_is_reported():
     """A tile that never publishes: its successor's bounded wait runs out,
     the launch completes and the result is flagged; the next launch is
