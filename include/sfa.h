@@ -187,7 +187,10 @@ int sfa_info(sfa_handle_t h, sfa_info_t *out);
  *   Handles with 16-bit ids (more than 256 reachable states) have empty DFA
  *   and MAPS tables and export CDFA16 and MAPS16 instead; their NC entries
  *   that lead to a point mapping {s -> p, all other states -> the sink} hold
- *   1 << 29 | s << 12 | p instead of an id.
+ *   1 << 29 | s << 12 | p instead of an id, and those that lead to a
+ *   set-point mapping {q in S -> p, all other states -> the sink} (S of two
+ *   or more states) hold 1 << 29 | 1 << 28 | sid << 12 | p, S being row sid
+ *   of SFA_TABLE_SETS.
  *   Writes min(bytes, table size); returns the table size in *size_out.
  */
 #define SFA_TABLE_CLASS 0
@@ -197,6 +200,9 @@ int sfa_info(sfa_handle_t h, sfa_info_t *out);
 #define SFA_TABLE_ORIG  4
 #define SFA_TABLE_CDFA16 5  /* uint16[nr * ncls]  kept DFA over classes (16-bit ids only) */
 #define SFA_TABLE_MAPS16 6  /* uint16[n_stored * nr] stored mappings (16-bit ids only) */
+#define SFA_TABLE_SETS   7  /* uint32[n_sets * ((nr + 31) / 32)] source sets of the set-point
+                               mappings, bit q of set s at word s * ((nr + 31) / 32) + q / 32
+                               (16-bit ids only) */
 int sfa_export(sfa_handle_t h, int32_t which, void *dst, size_t bytes, size_t *size_out);
 
 /* sfa_strerror -- static message for an SFA_* code. */

@@ -29,7 +29,7 @@ MODE_AUTO, MODE_SFA, MODE_SIM = 0, 1, 2
 COMPILE_HOST_ONLY, COMPILE_NO_BANK_TUNE = 1, 2
 STATUS_OK, STATUS_TIMEOUT = 0, 1
 DEBUG_SKIP_PUBLISH = 1
-TABLE_CLASS, TABLE_DFA, TABLE_NC, TABLE_MAPS, TABLE_ORIG, TABLE_CDFA16, TABLE_MAPS16 = 0, 1, 2, 3, 4, 5, 6
+TABLE_CLASS, TABLE_DFA, TABLE_NC, TABLE_MAPS, TABLE_ORIG, TABLE_CDFA16, TABLE_MAPS16, TABLE_SETS = 0, 1, 2, 3, 4, 5, 6, 7
 PLACE_SMEM_DFA, PLACE_SMEM_DFA_CLASSES, PLACE_GLOBAL_NC, PLACE_SMEM_VECTORS = 1, 2, 4, 8
 TILING_AUTO, TILING_CTA, TILING_WARP = 0, 1, 2
 SERVER_TIMING = 1
@@ -280,7 +280,8 @@ class Automaton:
         size = ctypes.c_size_t()
         _check(lib().sfa_export(self._h, which, None, 0, ctypes.byref(size)), "sfa_export")
         dtype = {TABLE_CLASS: np.uint8, TABLE_DFA: np.uint8, TABLE_NC: np.uint32, TABLE_MAPS: np.uint8,
-                 TABLE_ORIG: np.int32, TABLE_CDFA16: np.uint16, TABLE_MAPS16: np.uint16}[which]
+                 TABLE_ORIG: np.int32, TABLE_CDFA16: np.uint16, TABLE_MAPS16: np.uint16,
+                 TABLE_SETS: np.uint32}[which]
         buf = np.zeros(size.value // np.dtype(dtype).itemsize, dtype=dtype)
         _check(lib().sfa_export(self._h, which, buf.ctypes.data, buf.nbytes, ctypes.byref(size)), "sfa_export")
         return buf

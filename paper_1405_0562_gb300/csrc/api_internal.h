@@ -136,6 +136,11 @@ int launch_gather(const GatherDesc *d_descs, const uint32_t *d_unit0, uint32_t k
 // into the device's address space), or NULL.
 const uint8_t *device_readable(const uint8_t *h);
 
+// kernels_small.cu: the short-text kernel (one CTA, no scratch, no look-back)
+bool small_fits(uint64_t n);
+int launch_small(const sfa_dev::Tables &T, const uint8_t *text, uint64_t n, bool carry, sfa_result *out,
+                 cudaStream_t s);
+
 // regex.cpp
 int regex_to_dfa(const char *pattern, size_t len, uint32_t flags, int32_t cap, std::vector<int32_t> &delta,
                  std::vector<uint8_t> &accept, sfa_regex_info *info, size_t *err_pos);

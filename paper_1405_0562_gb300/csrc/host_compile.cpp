@@ -121,6 +121,11 @@ int build_wide(const int32_t *delta, int32_t nq, int32_t q0, const uint8_t *acce
     std::unordered_map<std::string, uint32_t, VecHash> ids;
     std::string g(2 * (size_t)nr, '\0');
     std::vector<uint16_t> gv(nr);
+    // source sets of set-point mappings (at most 4096: the id is 12 bits)
+    T.set_words = ((uint32_t)nr + 31) / 32;
+    T.setbits.clear();
+    std::unordered_map<std::string, uint32_t, VecHash> set_ids;
+    std::vector<uint32_t> sbits(T.set_words);
     for (int q = 0; q < nr; ++q) gv[q] = (uint16_t)q;
     T.maps16.insert(T.maps16.end(), gv.begin(), gv.end());
     ids.emplace(std::string(reinterpret_cast<const char *>(gv.data()), 2 * (size_t)nr), 0);
@@ -128,18 +133,36 @@ int build_wide(const int32_t *delta, int32_t nq, int32_t q0, const uint8_t *acce
     for (uint64_t head = 0; head < T.n_nc; ++head) {
         for (int c = 0; c < ncls; ++c) {
             const uint16_t *fm = T.maps16.data() + head * nr;
-            int live = 0, src = -1;
-            bool constant = true;
+            int live = 0, src = -1, img = -1;
+            bool constant = true, one_image = true;
+            std::fill(sbits.begin(), sbits.end(), 0u);
             for (int q = 0; q < nr; ++q) {
                 gv[q] = T.cdfa[(size_t)fm[q] * ncls + c];
                 constant &= gv[q] == gv[0];
                 if ((int)gv[q] != z) {
                     ++live;
                     src = q;
+                    one_image &= img < 0 || (int)gv[q] == img;
+                    img = gv[q];
+                    sbits[q >> 5] |= 1u << (q & 31);
                 }
             }
-            uint32_t e;
-            if (constant) {
+            uint32_t e = 0;
+            bool set_point = false;
+            if (!constant && z >= 0 && live >= 2 && one_image) {
+                const std::string key(reinterpret_cast<const char *>(sbits.data()), sbits.size() * 4);
+                auto it = set_ids.find(key);
+                if (it == set_ids.end() && set_ids.size() < (1u << WIDE_POINT_SHIFT)) {
+                    it = set_ids.emplace(key, (uint32_t)set_ids.size()).first;
+                    T.setbits.insert(T.setbits.end(), sbits.begin(), sbits.end());
+                }
+                if (it != set_ids.end()) {
+                    e = NC_POINT | NC_SET | it->second << WIDE_POINT_SHIFT | (uint32_t)img;
+                    set_point = true;
+                }
+            }
+            if (set_point) {
+            } else if (constant) {
                 e = gv[0];
             } else if (z >= 0 && live == 1) {
                 e = NC_POINT | (uint32_t)src << WIDE_POINT_SHIFT | gv[src];
@@ -186,27 +209,32 @@ int build_wide(const int32_t *delta, int32_t nq, int32_t q0, const uint8_t *acce
             cstack.push_back(c);
         }
     };
-    std::vector<uint64_t> preach(((size_t)nr * nr + 63) / 64, 0);
-    std::vector<uint32_t> pstack;
-    auto pmark = [&](uint32_t s_, uint32_t p_) {
-        const size_t k = (size_t)s_ * nr + p_;
+    // point mappings (s, p) and set-point mappings (S, p): pairs closed
+    // under p -> delta(p, sigma) (or the constant sink)
+    const size_t nsets = T.set_words ? T.setbits.size() / T.set_words : 0;
+    const size_t npair = ((size_t)nr + nsets) * nr;   // sources: states, then sets
+    std::vector<uint64_t> preach((npair + 63) / 64, 0);
+    std::vector<uint64_t> pstack;
+    auto pmark = [&](size_t s_, uint32_t p_) {
+        const size_t k = s_ * nr + p_;
         if (!(preach[k >> 6] >> (k & 63) & 1)) {
             preach[k >> 6] |= 1ull << (k & 63);
-            pstack.push_back((uint32_t)k);
+            pstack.push_back(k);
         }
     };
     for (uint32_t e : T.nc) {
         if (e & NC_POINT)
-            pmark((e >> WIDE_POINT_SHIFT) & 0xfffu, e & 0xfffu);
+            pmark((e & NC_SET ? (size_t)nr : 0) + ((e >> WIDE_POINT_SHIFT) & 0xfffu), e & 0xfffu);
         else if ((e & NC_ID_MASK) < (uint32_t)nr)
             cmark((int)(e & NC_ID_MASK));
     }
     T.n_points = 0;
     while (!pstack.empty()) {
-        const uint32_t k = pstack.back();
+        const uint64_t k = pstack.back();
         pstack.pop_back();
         ++T.n_points;
-        const uint32_t s_ = k / nr, p_ = k % nr;
+        const size_t s_ = k / nr;
+        const uint32_t p_ = (uint32_t)(k % nr);
         for (int c = 0; c < ncls; ++c) {
             const uint32_t np = T.cdfa[(size_t)p_ * ncls + c];
             if ((int)np == z) cmark(z);

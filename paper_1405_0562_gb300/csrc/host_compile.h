@@ -12,6 +12,7 @@ enum AccClass : uint32_t { ACC_NONE = 0, ACC_ALL = 1, ACC_MIXED = 2 };
 
 constexpr uint32_t NC_ID_MASK = 0x1fffffffu;   // bit 29 is the device's point flag
 constexpr uint32_t NC_POINT = 1u << 29;
+constexpr uint32_t NC_SET = 1u << 28;           // with NC_POINT: the source field is a set id
 constexpr int NC_ACC_SHIFT = 30;
 constexpr uint32_t DEFAULT_CAP = 65536;
 constexpr int SIM_MAX_STATES = 256;
@@ -44,7 +45,12 @@ struct HostTables {
     int32_t sink = -1;             // wide: the absorbing non-final state, or -1
     std::vector<uint16_t> cdfa;    // wide: [nr*ncls] kept DFA over classes
     std::vector<uint16_t> maps16;  // wide: [n_nc*nr] f(q) of each stored non-constant state
-    uint64_t n_points = 0;         // wide: point mappings reachable from f_I (not stored)
+    uint64_t n_points = 0;         // wide: point and set-point mappings reachable from f_I (not stored)
+    // wide: the source sets of the set-point mappings {q in S -> p, others ->
+    // sink} (|S| >= 2; entries NC_POINT | NC_SET | sid << 12 | p), bit q of
+    // set sid at setbits[sid * set_words + q / 32]
+    std::vector<uint32_t> setbits;
+    uint32_t set_words = 0;
 };
 
 // Returns SFA_OK or an SFA_ERR_* code (see sfa.h for the rules).  tune_banks:

@@ -54,12 +54,19 @@ int blocks_per_sm(const void *k, int threads, size_t smem) {
 // The device's point-mapping encoding of the non-constant rows (see
 // sfa_types.h): with an absorbing non-final state z (the sink), every entry
 // whose target maps all states but one, s, to z carries s and the image p
-// of s instead of the target's id, and pid[s*nr + p] gives the id back.
-// Returns the sink, or NO_SINK (no such state, simulation mode, or 256 kept
-// states, where a byte-wide "no point" marker would be a state).
-uint32_t point_encoding(const HostTables &H, std::vector<uint32_t> &nc, std::vector<uint32_t> &pid) {
+// of s instead of the target's id, and pid[s*nr + p] gives the id back; an
+// entry whose target maps a set S of two or more states to one p and the
+// rest to z carries NC_SET, the id of S and p (set-point mapping), with
+// spid[sid*nr + p] the id and setbits the sets (at most 255 of them; past
+// that the targets keep their ids).  Returns the sink, or NO_SINK (no such
+// state, simulation mode, or 256 kept states, where a byte-wide "no point"
+// marker would be a state).
+uint32_t point_encoding(const HostTables &H, std::vector<uint32_t> &nc, std::vector<uint32_t> &pid,
+                        std::vector<uint32_t> &setbits, std::vector<uint32_t> &spid) {
     nc = H.nc;
     pid.clear();
+    setbits.clear();
+    spid.clear();
     const int nr = H.nr;
     if (H.mode != SFA_MODE_SFA || nr < 2 || nr > 255 || H.n_nc == 0) return sfa_dev::NO_SINK;
     int z = -1;
@@ -69,30 +76,56 @@ uint32_t point_encoding(const HostTables &H, std::vector<uint32_t> &nc, std::vec
         if (absorbing) z = q;
     }
     if (z < 0) return sfa_dev::NO_SINK;
-    std::vector<int32_t> src(H.n_nc, -1), img(H.n_nc, 0);
+    const uint32_t words = ((uint32_t)nr + 31) / 32;
+    std::vector<int32_t> src(H.n_nc, -1), img(H.n_nc, 0), set_of(H.n_nc, -1);
+    std::map<std::vector<uint32_t>, int32_t> set_id;
     bool any = false;
     for (uint64_t i = 0; i < H.n_nc; ++i) {
         const uint8_t *f = H.maps.data() + i * nr;
-        int live = 0, s = -1;
+        int live = 0, s = -1, p = -1;
+        bool one_image = true;
+        std::vector<uint32_t> bits(words, 0);
         for (int q = 0; q < nr; ++q)
             if (f[q] != z) {
                 ++live;
                 s = q;
+                one_image &= p < 0 || f[q] == p;
+                p = f[q];
+                bits[q >> 5] |= 1u << (q & 31);
             }
         if (live == 1) {
             src[i] = s;
             img[i] = f[s];
             any = true;
+        } else if (live >= 2 && one_image) {
+            auto it = set_id.find(bits);
+            if (it == set_id.end()) {
+                if (set_id.size() >= 255) continue;
+                it = set_id.emplace(bits, (int32_t)set_id.size()).first;
+            }
+            set_of[i] = it->second;
+            img[i] = p;
+            any = true;
         }
     }
     if (!any) return sfa_dev::NO_SINK;
     pid.assign((size_t)nr * nr, 0);
-    for (uint64_t i = 0; i < H.n_nc; ++i)
+    spid.assign(set_id.size() * (size_t)nr, 0);
+    setbits.assign(set_id.size() * words, 0);
+    for (const auto &kv : set_id) std::copy(kv.first.begin(), kv.first.end(), setbits.begin() + (size_t)kv.second * words);
+    for (uint64_t i = 0; i < H.n_nc; ++i) {
         if (src[i] >= 0) pid[(size_t)src[i] * nr + img[i]] = (uint32_t)(nr + i);
+        if (set_of[i] >= 0) spid[(size_t)set_of[i] * nr + img[i]] = (uint32_t)(nr + i);
+    }
     for (uint32_t &e : nc) {
         const uint32_t id = e & sfa_dev::NC_ID_MASK;
-        if (id >= (uint32_t)nr && src[id - nr] >= 0)
-            e = (e & ~sfa_dev::NC_ID_MASK) | sfa_dev::NC_POINT | (uint32_t)src[id - nr] << 8 | (uint32_t)img[id - nr];
+        if (id < (uint32_t)nr) continue;
+        const uint64_t k = id - nr;
+        if (src[k] >= 0)
+            e = (e & ~sfa_dev::NC_ID_MASK) | sfa_dev::NC_POINT | (uint32_t)src[k] << 8 | (uint32_t)img[k];
+        else if (set_of[k] >= 0)
+            e = (e & ~sfa_dev::NC_ID_MASK) | sfa_dev::NC_POINT | sfa_dev::NC_SET | (uint32_t)set_of[k] << 8 |
+                (uint32_t)img[k];
     }
     return (uint32_t)z;
 }
@@ -109,7 +142,8 @@ int upload_tables_wide(sfa_handle *h) {
     size_t off_maps = align_up(off_nc + H.nc.size() * 4, 256);
     size_t off_orig = align_up(off_maps + H.maps16.size() * 2, 256);
     size_t off_kept = align_up(off_orig + nr * 4, 256);
-    size_t total = align_up(off_kept + (size_t)H.nq_in * 4, 256);
+    size_t off_sets = align_up(off_kept + (size_t)H.nq_in * 4, 256);
+    size_t total = align_up(off_sets + H.setbits.size() * 4, 256);
     std::vector<uint8_t> img(total, 0);
     std::memcpy(img.data() + off_cdfa, H.cdfa.data(), H.cdfa.size() * 2);
     std::memcpy(img.data() + off_cls, H.cls, 256);
@@ -117,6 +151,7 @@ int upload_tables_wide(sfa_handle *h) {
     if (!H.maps16.empty()) std::memcpy(img.data() + off_maps, H.maps16.data(), H.maps16.size() * 2);
     std::memcpy(img.data() + off_orig, H.orig_of.data(), nr * 4);
     std::memcpy(img.data() + off_kept, H.kept_of.data(), (size_t)H.nq_in * 4);
+    if (!H.setbits.empty()) std::memcpy(img.data() + off_sets, H.setbits.data(), H.setbits.size() * 4);
     CK(cudaMalloc(&h->d_tables, total));
     cudaError_t e = cudaMemcpy(h->d_tables, img.data(), total, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
@@ -127,6 +162,8 @@ int upload_tables_wide(sfa_handle *h) {
     h->table_bytes = total;
     Tables &T = h->dev;
     T = Tables{};
+    T.setbits = H.setbits.empty() ? nullptr : reinterpret_cast<const uint32_t *>(h->d_tables + off_sets);
+    T.set_words = H.set_words;
     T.cdfa = reinterpret_cast<const uint16_t *>(h->d_tables + off_cdfa);
     T.cls = h->d_tables + off_cls;
     T.nc = reinterpret_cast<const uint32_t *>(h->d_tables + off_nc);
@@ -148,8 +185,8 @@ int upload_tables(sfa_handle *h) {
     const auto &H = h->host;
     if (H.wide) return upload_tables_wide(h);
     const size_t nr = (size_t)H.nr;
-    std::vector<uint32_t> nc, pid;
-    const uint32_t sink = point_encoding(H, nc, pid);
+    std::vector<uint32_t> nc, pid, setbits, spid;
+    const uint32_t sink = point_encoding(H, nc, pid, setbits, spid);
     size_t off_dfa = 0;
     size_t off_cls = align_up(off_dfa + nr * 256, 256);
     size_t off_nc = align_up(off_cls + 256, 256);
@@ -157,12 +194,16 @@ int upload_tables(sfa_handle *h) {
     size_t off_orig = align_up(off_maps + H.maps.size(), 256);
     size_t off_kept = align_up(off_orig + nr * 4, 256);
     size_t off_pid = align_up(off_kept + (size_t)H.nq_in * 4, 256);
-    size_t total = align_up(off_pid + pid.size() * 4, 256);
+    size_t off_sets = align_up(off_pid + pid.size() * 4, 256);
+    size_t off_spid = align_up(off_sets + setbits.size() * 4, 256);
+    size_t total = align_up(off_spid + spid.size() * 4, 256);
     std::vector<uint8_t> img(total, 0);
     std::memcpy(img.data() + off_dfa, H.dfa.data(), H.dfa.size());
     std::memcpy(img.data() + off_cls, H.cls, 256);
     if (!nc.empty()) std::memcpy(img.data() + off_nc, nc.data(), nc.size() * 4);
     if (!pid.empty()) std::memcpy(img.data() + off_pid, pid.data(), pid.size() * 4);
+    if (!setbits.empty()) std::memcpy(img.data() + off_sets, setbits.data(), setbits.size() * 4);
+    if (!spid.empty()) std::memcpy(img.data() + off_spid, spid.data(), spid.size() * 4);
     if (!H.maps.empty()) std::memcpy(img.data() + off_maps, H.maps.data(), H.maps.size());
     std::memcpy(img.data() + off_orig, H.orig_of.data(), nr * 4);
     std::memcpy(img.data() + off_kept, H.kept_of.data(), (size_t)H.nq_in * 4);
@@ -183,6 +224,9 @@ int upload_tables(sfa_handle *h) {
     T.orig_of = reinterpret_cast<const int32_t *>(h->d_tables + off_orig);
     T.kept_of = reinterpret_cast<const int32_t *>(h->d_tables + off_kept);
     T.pid = pid.empty() ? nullptr : reinterpret_cast<const uint32_t *>(h->d_tables + off_pid);
+    T.setbits = setbits.empty() ? nullptr : reinterpret_cast<const uint32_t *>(h->d_tables + off_sets);
+    T.spid = spid.empty() ? nullptr : reinterpret_cast<const uint32_t *>(h->d_tables + off_spid);
+    T.set_words = ((uint32_t)nr + 31) / 32;
     T.sink = sink;
     T.nr = H.nr;
     T.ncls = H.ncls;
@@ -442,6 +486,13 @@ int match_impl(sfa_handle *h, const uint8_t *d_text, uint64_t n, sfa_result *d_o
     // the slice mapping is composed from CTA-tile aggregates of byte ids
     if (d_map && o && o->tiling == SFA_TILING_WARP) return SFA_ERR_INVALID;
     if (d_map && h->host.wide) return SFA_ERR_UNSUPPORTED;
+    // a short text with the automatic shape: one CTA, no scratch (its
+    // latency is a kernel launch and the text's dependent lookups)
+    const bool shape_given = o && (o->chunk_bytes || o->block_threads || o->chains || o->max_ctas ||
+                                   o->forced_chunks || o->debug_flags || o->tiling);
+    if (!d_map && !shape_given && h->host.mode == SFA_MODE_SFA && !h->host.wide && h->host.nr <= 255 &&
+        small_fits(n))
+        return launch_small(h->dev, d_text, n, carry, d_out, s);
     Shape sh;
     int rc = choose_shape(h, n, o, sh);
     if (rc) return rc;
@@ -591,6 +642,7 @@ int sfa_export(sfa_handle_t h, int32_t which, void *dst, size_t bytes, size_t *s
         case SFA_TABLE_ORIG: src = H.orig_of.data(); sz = H.orig_of.size() * 4; break;
         case SFA_TABLE_CDFA16: src = H.cdfa.data(); sz = H.cdfa.size() * 2; break;
         case SFA_TABLE_MAPS16: src = H.maps16.data(); sz = H.maps16.size() * 2; break;
+        case SFA_TABLE_SETS: src = H.setbits.data(); sz = H.setbits.size() * 4; break;
         default: return SFA_ERR_INVALID;
     }
     if (size_out) *size_out = sz;

@@ -214,8 +214,21 @@ template <bool WIDE>
 struct Pt {
     static constexpr uint32_t SHIFT = WIDE ? 12u : 8u;
     static constexpr uint32_t MASK = (1u << SHIFT) - 1u;
-    static constexpr uint32_t KEEP = NC_POINT | ((1u << (2 * SHIFT)) - 1u);   // the flag and both fields
+    static constexpr uint32_t KEEP = NC_POINT | NC_SET | ((1u << (2 * SHIFT)) - 1u);   // the flags and both fields
 };
+
+// q in the source set sid of a set-point mapping
+__device__ __forceinline__ bool in_set(const Tables &T, uint32_t sid, uint32_t q) {
+    return (__ldg(T.setbits + (size_t)sid * T.set_words + (q >> 5)) >> (q & 31u)) & 1u;
+}
+
+// The point source a chunk keeps for pass 2 (16 bits): its source state s,
+// or PS_SET | the id of its source set; 0xffff: none.
+template <bool WIDE>
+__device__ __forceinline__ uint32_t point_source_of(uint32_t f) {
+    const uint32_t fld = (f >> Pt<WIDE>::SHIFT) & Pt<WIDE>::MASK;
+    return f & NC_SET ? PS_SET | fld : fld;
+}
 
 // one symbol of Alg. 5 in the D-SFA: f <- delta_s[f, sigma].
 // Point mappings {s -> p, others -> sink}: f = NC_POINT | s << SHIFT | p, and
@@ -254,9 +267,11 @@ __device__ __forceinline__ void sfa_step(Chain &s, uint32_t b, int32_t j, const 
 // The count of a chunk entered in state v, from its pass-1 record: the DFA
 // rerun over [lo, lo + lm] (rerun: its value, or 0 when it is added later),
 // then the positions after lm -- all of them if the chunk never became a
-// point mapping, else only for the entering state ps.
-__device__ __forceinline__ uint32_t chunk_count_after(const Chain &c, uint32_t v, uint32_t ps) {
-    return ps == NO_POINT || v == ps ? c.cnt - c.snap : 0u;
+// point mapping, else only for the entering state ps (or a state of the
+// source set, PS_SET | sid).
+__device__ __forceinline__ uint32_t chunk_count_after(const Chain &c, uint32_t v, uint32_t ps, const Tables &T) {
+    const bool live = ps == NO_POINT || (ps & PS_SET ? in_set(T, ps & ~PS_SET, v) : v == ps);
+    return live ? c.cnt - c.snap : 0u;
 }
 
 // 4 symbols of a constant-state chunk, keeping the largest state seen
@@ -530,11 +545,16 @@ __device__ __forceinline__ uint32_t apply_map(uint32_t f, uint32_t v, const uint
     return f < nr ? f : (uint32_t)mtab[(size_t)(f - nr) * nr + v];
 }
 // 16-bit ids: a chunk may also end as a point mapping {s -> p, others ->
-// sink}, kept in its encoded form (point mappings are not stored)
+// sink} or a set-point mapping {S -> p, others -> sink}, kept in its encoded
+// form (neither is stored)
 __device__ __forceinline__ uint32_t apply_map(uint32_t f, uint32_t v, const uint16_t *mtab, uint32_t nr,
-                                              uint32_t sink) {
+                                              uint32_t sink, const Tables &T) {
     if (f < nr) return f;
-    if (f & NC_POINT) return v == ((f >> Pt<true>::SHIFT) & Pt<true>::MASK) ? (f & Pt<true>::MASK) : sink;
+    if (f & NC_POINT) {
+        const uint32_t fld = (f >> Pt<true>::SHIFT) & Pt<true>::MASK;
+        const bool live = f & NC_SET ? in_set(T, fld, v) : v == fld;
+        return live ? (f & Pt<true>::MASK) : sink;
+    }
     return mtab[(size_t)(f - nr) * nr + v];
 }
 
@@ -720,7 +740,7 @@ __global__ void __launch_bounds__(THREADS, (min_ctas_per_sm<THREADS, CH, SIMNQ, 
     static_assert(!WT || (!BATCH && CH == 1), "warp tiles: one text, one chunk per thread");
     static_assert(!WIDE || (!WT && !BATCH && SIMNQ == 0), "16-bit ids: single texts, CTA tiles, D-SFA mode");
     constexpr int NQ = SIMNQ > 0 ? SIMNQ : 4;
-    constexpr uint32_t NO_PT = WIDE ? 0xffffu : 0xffu;   // "no point source" in the extra rows
+    constexpr uint32_t NO_PT = 0xffffu;   // "no point source" in the extra rows
     extern __shared__ __align__(128) uint8_t smem[];
     const uint32_t nr_max = S.nr_max;
     const uint32_t lcls = WIDE ? tab.ncls : 0u;   // class count of the layout (16-bit ids)
@@ -746,7 +766,7 @@ __global__ void __launch_bounds__(THREADS, (min_ctas_per_sm<THREADS, CH, SIMNQ, 
     const uint32_t bar0 = smem_addr(smem + L::bar_off(nr_max, lcls)) + (uint32_t)warp * STAGES * 8;
     uint8_t *s_box = smem + L::stage_off(nr_max, lcls) + (size_t)warp * STAGES * CH * BOX;
     uint8_t *s_extra = smem + L::extra_off(nr_max, lcls) + (size_t)warp * STAGES * CH * SLICE;
-    SID *s_psrc = reinterpret_cast<SID *>(s_extra);   // point sources after pass 1 ([round][lane])
+    uint16_t *s_psrc = reinterpret_cast<uint16_t *>(s_extra);   // point sources after pass 1 ([round][lane])
     // the point source of this lane's chunk of round c (after pass 1)
     auto point_src = [&](int c) -> uint32_t {
         const uint32_t v = s_psrc[c * 32 + lane];
@@ -871,7 +891,7 @@ __global__ void __launch_bounds__(THREADS, (min_ctas_per_sm<THREADS, CH, SIMNQ, 
         // a chunk or group mapping applied to a state
         auto amap = [&](uint32_t f, uint32_t v) -> uint32_t {
             if constexpr (WIDE)
-                return apply_map(f, v, T.maps16, nr, T.sink);
+                return apply_map(f, v, T.maps16, nr, T.sink, T);
             else if constexpr (SIMNQ > 0 && BATCH)
                 return f < nr ? f : (uint32_t)mtab[(size_t)(f - nr) * vstride + v];
             else
@@ -1185,16 +1205,17 @@ __global__ void __launch_bounds__(THREADS, (min_ctas_per_sm<THREADS, CH, SIMNQ, 
             // its D-SFA id (the constant sink once p is there) for the scan
             uint32_t ps = NO_PT;
             if (!SIMNQ && (ch[c].f & NC_POINT)) {
-                ps = (ch[c].f >> P::SHIFT) & P::MASK;
+                ps = point_source_of<WIDE>(ch[c].f);
                 const uint32_t p = ch[c].f & P::MASK;
-                // byte ids: the stored id of {ps -> p}; 16-bit ids keep the
-                // encoded form (point mappings are not stored)
+                const uint32_t fld = ps & ~PS_SET;
+                // byte ids: the stored id of {ps -> p} or {S -> p}; 16-bit
+                // ids keep the encoded form (neither is stored)
                 if constexpr (WIDE)
                     ch[c].f = p == T.sink ? p : ch[c].f;
                 else
-                    ch[c].f = p == T.sink ? p : __ldg(T.pid + ps * nr + p);
+                    ch[c].f = p == T.sink ? p : __ldg((ps & PS_SET ? T.spid : T.pid) + fld * nr + p);
             }
-            s_psrc[c * 32 + lane] = (SID)ps;
+            s_psrc[c * 32 + lane] = (uint16_t)ps;
             if (SIMNQ) sim_compact<NQ>(V[c], ch[c]);
             if (SIMNQ && V[c].mode != SIM_CONST) {
                 // keep the vector for the scan: id nr + global chunk index
@@ -1265,7 +1286,7 @@ __global__ void __launch_bounds__(THREADS, (min_ctas_per_sm<THREADS, CH, SIMNQ, 
             unsigned long long tsum = ch[0].cnt;
             if (ch[0].lm >= 0)
                 tsum = dfa_count<WIDE>(text, lo[0], lo[0] + (uint64_t)ch[0].lm + 1, v, R, A) +
-                       chunk_count_after(ch[0], v, point_src(0));
+                       chunk_count_after(ch[0], v, point_src(0), T);
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) tsum += __shfl_down_sync(0xffffffffu, tsum, o);
             if (lane == 0) finish_tile(S, T, d, ts, out, tsum, local, incl);
@@ -1408,7 +1429,7 @@ __global__ void __launch_bounds__(THREADS, (min_ctas_per_sm<THREADS, CH, SIMNQ, 
                 // positions after its last mixed one now
                 const bool deferred = DEFER && c == 0 && tid == 0 && s_misc->dfr_valid;
                 cc = (deferred ? 0u : dfa_count<WIDE>(text, lo[c], lo[c] + (uint64_t)ch[c].lm + 1, v, R, A)) +
-                     chunk_count_after(ch[c], v, point_src(c));
+                     chunk_count_after(ch[c], v, point_src(c), T);
             }
             tsum += cc;
         }

@@ -20,8 +20,13 @@ namespace sfa_dev {
 // lookup per byte) until it ends or p falls into the sink.
 constexpr uint32_t NC_ID_MASK = 0x1fffffffu;
 constexpr uint32_t NC_POINT = 1u << 29;
+// With NC_POINT, NC_SET marks a set-point mapping {q in S -> p, every other
+// q -> sink} (|S| >= 2): the source field holds the id of the set S (a row
+// of Tables::setbits) instead of a state.
+constexpr uint32_t NC_SET = 1u << 28;
 constexpr uint32_t NO_SINK = 0xffffffffu;
-constexpr uint32_t NO_POINT = 0xffffffffu;   // a chunk's point source: none (0xff when kept as a byte)
+constexpr uint32_t NO_POINT = 0xffffffffu;   // a chunk's point source: none (0xffff when kept in 16 bits)
+constexpr uint32_t PS_SET = 0x8000u;         // a kept point source that is a set id
 constexpr uint32_t ACC_ALL = 1, ACC_MIXED = 2;
 
 // look-back descriptor: flag in bits 62..63, value (a kept DFA state) below
@@ -36,6 +41,9 @@ struct Tables {
     const int32_t *orig_of;    // [nr]
     const int32_t *kept_of;    // [nq_in]
     const uint32_t *pid;       // [nr*nr] id of the point mapping {s -> p} at s*nr + p (sink != NO_SINK)
+    const uint32_t *setbits;   // [n_sets*set_words] the source set of each set-point id, bit q of q
+    const uint32_t *spid;      // byte ids: [n_sets*nr] id of the set-point mapping {S -> p} at sid*nr + p
+    uint32_t set_words;        // 32-bit words per set: (nr + 31) / 32
     // more than 256 kept states (16-bit ids): dfa and maps are unused
     const uint16_t *cdfa;      // [nr*ncls] kept DFA over byte classes
     const uint16_t *maps16;    // [n_nc*nr]  stored non-constant mappings

@@ -109,6 +109,38 @@ def test_launch_shapes(threads, chains, chunk):
         assert gpu_match(a, t, block_threads=threads, chains=chains, chunk_bytes=chunk) == expect(d, t), name
 
 
+SMALL_LENS = [0, 1, 2, 15, 16, 17, 31, 63, 64, 65, 1000, 1023, 1024, 1025, 16383, 16384, 16385, 16400,
+              16401, 32768, 49151, 65519, 65535, 65536]
+
+
+@pytest.mark.parametrize("name", sorted(AUTOMATA))
+def test_short_texts_one_cta(name):
+    """Texts up to 64 KiB with the automatic shape take the one-CTA kernel
+    (no scratch, no look-back): every length around its chunk sizes (16 to
+    64 bytes per thread) and its 64 KiB limit, every start offset modulo 16,
+    and Lemma 1 streaming with short pieces.  Simulation-mode handles and
+    explicit shapes keep the persistent kernel."""
+    sfa = sfa_mod()
+    d = AUTOMATA[name]()
+    a = sfa.Automaton.from_dfa(d)
+    base = text_for(d, (64 << 10) + 64, seed=len(name))
+    dev = torch.from_numpy(base).cuda()
+    for n in SMALL_LENS:
+        for off in (0, 1, 7, 15):
+            if off + n > base.size:
+                continue
+            out = a.match(dev[off:off + n])
+            torch.cuda.synchronize()
+            assert sfa.decode(out)[0] == expect(d, base[off:off + n]), (name, n, off)
+    # Lemma 1 pieces of a few hundred bytes, then one past the limit
+    cuts = [0, 5, 300, 301, 4000, 20000, 65536 + 3, base.size]
+    out = a.match(dev[:cuts[1]])
+    for i in range(1, len(cuts) - 1):
+        a.match_continue(dev[cuts[i]:cuts[i + 1]], out)
+    torch.cuda.synchronize()
+    assert sfa.decode(out)[0] == expect(d, base)
+
+
 @pytest.mark.parametrize("name", ["ab_star", "r5", "ac_set", "T4", "rand8", "kmp", "one_state"])
 @pytest.mark.parametrize("n", [0, 1, 33, 4096, 100_003, 1 << 21])
 def test_tilings_agree(name, n):

@@ -340,3 +340,44 @@ def test_compile_sample_arguments():
     assert L.sfa_compile_sample(delta.ctypes.data, d.nq, d.q0, acc.ctypes.data, ctypes.byref(opts),
                                 short.ctypes.data, short.size, ctypes.byref(h)) == sfa.OK
     L.sfa_destroy(h)
+
+
+def test_wide_set_point_entries_are_the_mappings_they_stand_for():
+    """16-bit-id tables: every row entry of a stored mapping f on class c is
+    f . delta^c -- a constant, a point mapping (NC_POINT, source s), a
+    set-point mapping (NC_POINT | NC_SET, source set from SFA_TABLE_SETS) or
+    a stored mapping -- recomputed here from the exported DFA and mappings."""
+    for d in (W.dfa_ra(150), W.dfa_rn(140)):
+        a = host(d)
+        info = a.info()
+        assert info["id_bits"] == 16
+        nr, ncls = info["n_reachable"], info["ncls"]
+        cdfa = a.export(sfa.TABLE_CDFA16).reshape(nr, ncls).astype(np.int64)
+        maps = a.export(sfa.TABLE_MAPS16).reshape(-1, nr).astype(np.int64)
+        nc = a.export(sfa.TABLE_NC).reshape(-1, ncls)
+        words = (nr + 31) // 32
+        sets = a.export(sfa.TABLE_SETS).reshape(-1, words) if d.name.startswith("r_a") else None
+        sink = [q for q in range(nr) if (cdfa[q] == q).all() and q < nr - info["n_accepting"]][0]
+        n_sets = 0
+        for h in range(maps.shape[0]):
+            for c in range(ncls):
+                g = cdfa[maps[h], c]
+                e = int(nc[h, c])
+                if e & (1 << 29):
+                    p = e & 0xFFF
+                    fld = (e >> 12) & 0xFFF
+                    if e & (1 << 28):
+                        n_sets += 1
+                        src = {q for q in range(nr) if sets[fld][q >> 5] >> (q & 31) & 1}
+                        assert len(src) >= 2
+                    else:
+                        src = {fld}
+                    want = np.array([p if q in src else sink for q in range(nr)])
+                    assert np.array_equal(g, want), (d.name, h, c)
+                else:
+                    ident = e & 0x1FFFFFFF
+                    if ident < nr:
+                        assert (g == ident).all()
+                    else:
+                        assert np.array_equal(g, maps[ident - nr])
+        assert (n_sets > 0) == d.name.startswith("r_a")
