@@ -1,10 +1,13 @@
 // The short-text form of Alg. 5: one CTA matches a text of up to
 // SMALL_THREADS * SMALL_CHUNK bytes with no scratch memory, no bulk copies
 // and no look-back, for the latency of single short matches.  Each thread
-// loads its chunk (at most SMALL_CHUNK + 15 bytes) into registers, runs the
-// SFA from f_I over it, and after the CTA's scan of the chunk mappings
-// (Lemma 1) recounts the prefix whose acceptance depended on the entering
-// state from those registers.  D-SFA handles with byte state ids only.
+// loads its chunk into shared memory (word k of thread t at k * SMALL_THREADS
+// + t, so that a warp's reads of one word are conflict-free), runs the SFA
+// from f_I over it, and after the CTA's scan of the chunk mappings (Lemma 1)
+// recounts the prefix whose acceptance depended on the entering state.  D-SFA
+// handles with byte state ids only.  Every loop over text bytes is rolled: a
+// launch of a few microseconds lands on an SM whose instruction cache does
+// not hold this kernel, so its code is kept short.
 #include <algorithm>
 
 #include "api_internal.h"
@@ -25,15 +28,10 @@ struct SmallLayout {
     static SFA_HD size_t gpre_off(uint32_t nr) { return gval_off(nr) + G * 4; }
     static SFA_HD size_t red_off(uint32_t nr) { return gpre_off(nr) + G * 4; }
     static SFA_HD size_t misc_off(uint32_t nr) { return red_off(nr) + G * 8; }
-    static SFA_HD size_t gvec_off(uint32_t nr) { return misc_off(nr) + 16; }
+    static SFA_HD size_t txt_off(uint32_t nr) { return misc_off(nr) + 16; }
+    static SFA_HD size_t gvec_off(uint32_t nr) { return txt_off(nr) + (size_t)SMALL_WORDS * SMALL_THREADS * 4; }
     static SFA_HD size_t bytes(uint32_t nr) { return a16(gvec_off(nr) + (size_t)G * nr); }
 };
-
-// byte j of a chunk held in registers (j a compile-time constant after
-// unrolling)
-__device__ __forceinline__ uint32_t reg_byte(const uint32_t (&w)[SMALL_WORDS], int j) {
-    return (w[j >> 2] >> (8 * (j & 3))) & 0xffu;
-}
 
 __global__ void __launch_bounds__(SMALL_THREADS) sfa_small_kernel(Tables T, const uint8_t *text, uint64_t n,
                                                                   uint32_t chunk, uint32_t origin, uint32_t carry,
@@ -49,35 +47,43 @@ __global__ void __launch_bounds__(SMALL_THREADS) sfa_small_kernel(Tables T, cons
     uint32_t *s_gpre = reinterpret_cast<uint32_t *>(smem + L::gpre_off(nr));
     unsigned long long *s_red = reinterpret_cast<unsigned long long *>(smem + L::red_off(nr));
     uint32_t *s_misc = reinterpret_cast<uint32_t *>(smem + L::misc_off(nr));
+    uint32_t *s_txt = reinterpret_cast<uint32_t *>(smem + L::txt_off(nr));
     uint8_t *s_gvec = smem + L::gvec_off(nr);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t lanemask_lt = (1u << lane) - 1u;
     Rows<false> R;
     R.d = s_dfa;
 
-    // this thread's chunk: [0, origin + chunk) for chunk 0, then chunks of
-    // `chunk` bytes from the first 16-byte boundary (Theorem 3: any division)
-    const uint64_t lo = tid == 0 ? 0 : (uint64_t)origin + (uint64_t)tid * chunk;
-    const uint64_t e = (uint64_t)origin + (uint64_t)(tid + 1) * chunk;
-    const uint64_t hi = e < n ? e : n;
-    const uint32_t len = lo < hi ? (uint32_t)(hi - lo) : 0u;
-    uint32_t w[SMALL_WORDS];
+    // This thread's window of the text, from a 16-byte boundary: offsets are
+    // taken from the boundary at or below text[0] (head bytes before it).
+    // Chunk 0 is [0, origin + chunk) (window bytes [head, 16 + chunk)), chunk
+    // t > 0 is [origin + t * chunk, origin + (t + 1) * chunk) (Theorem 3: any
+    // division); window bytes [jlo, jhi) are the chunk's.
+    const uint32_t head = origin ? 16u - origin : 0u, o16 = head + origin;
+    const uint64_t vs = tid == 0 ? 0 : (uint64_t)o16 + (uint64_t)tid * chunk;
+    const uint64_t ve_c = (uint64_t)o16 + (uint64_t)(tid + 1) * chunk, ve_t = (uint64_t)head + n;
+    const uint64_t ve = ve_c < ve_t ? ve_c : ve_t;
+    const uint32_t jlo = tid == 0 ? head : 0u;
+    const uint32_t jhi = ve > vs ? (uint32_t)(ve - vs) : 0u;
 #pragma unroll
-    for (int i = 0; i < SMALL_WORDS; ++i) w[i] = 0;
-    if (tid > 0 && len == chunk && (chunk & 15u) == 0 && ((reinterpret_cast<uintptr_t>(text) + lo) & 15u) == 0) {
+    for (uint32_t u = 0; u < (uint32_t)SMALL_WORDS / 4; ++u) {
+        const uint32_t a = 16 * u;
+        uint4 x = make_uint4(0, 0, 0, 0);
+        if (jlo <= a && a + 16 <= jhi) {
+            x = ldg128(text + (vs + a - head));
+        } else if (a < jhi && a + 16 > jlo) {   // the text's first or last partial 16 bytes
+            uint32_t wd[4] = {0, 0, 0, 0};
 #pragma unroll
-        for (int u = 0; u < SMALL_CHUNK / 16; ++u)
-            if ((uint32_t)(16 * u) < len) {
-                const uint4 v = ldg128(text + lo + 16 * u);
-                w[4 * u] = v.x;
-                w[4 * u + 1] = v.y;
-                w[4 * u + 2] = v.z;
-                w[4 * u + 3] = v.w;
-            }
-    } else {
-#pragma unroll
-        for (int j = 0; j < SMALL_WORDS * 4; ++j)
-            if ((uint32_t)j < len) w[j >> 2] |= (uint32_t)__ldg(text + lo + j) << (8 * (j & 3));
+            for (uint32_t b = 0; b < 16; ++b)
+                if (a + b >= jlo && a + b < jhi) wd[b >> 2] |= (uint32_t)__ldg(text + (vs + a + b - head)) << (8 * (b & 3));
+            x = make_uint4(wd[0], wd[1], wd[2], wd[3]);
+        }
+        if (a < jhi) {
+            s_txt[(4 * u + 0) * SMALL_THREADS + tid] = x.x;
+            s_txt[(4 * u + 1) * SMALL_THREADS + tid] = x.y;
+            s_txt[(4 * u + 2) * SMALL_THREADS + tid] = x.z;
+            s_txt[(4 * u + 3) * SMALL_THREADS + tid] = x.w;
+        }
     }
     // the DFA rows (ROWB apart) and the class table, every load in flight
     {
@@ -89,6 +95,7 @@ __global__ void __launch_bounds__(SMALL_THREADS) sfa_small_kernel(Tables T, cons
             const uint32_t i = u * SMALL_THREADS + tid;
             if (i < n16) v[u] = __ldg(src + i);
         }
+#pragma unroll 1
         for (uint32_t i = 2 * SMALL_THREADS + tid; i < n16; i += SMALL_THREADS) {
             const uint4 x = __ldg(src + i);
             uint2 *dst = reinterpret_cast<uint2 *>(s_dfa + (i >> 4) * ROWB + (i & 15) * 16);
@@ -108,17 +115,22 @@ __global__ void __launch_bounds__(SMALL_THREADS) sfa_small_kernel(Tables T, cons
     }
     __syncthreads();
 
-    // pass 1: the chunk from f_I
+    // pass 1: the chunk from f_I, one word (4 bytes) per iteration
     Chain ch;
     ch.f = T.ident;
     ch.cnt = 0;
     ch.snap = 0;
     ch.lm = -1;
-    // (predicated, not a break: the loop unrolls and the chunk stays in
-    // registers)
+    const uint32_t kend = (jhi + 3) >> 2;
+#pragma unroll 1
+    for (uint32_t k = jlo >> 2; k < kend; ++k) {
+        const uint32_t x = s_txt[k * SMALL_THREADS + tid];
 #pragma unroll
-    for (int j = 0; j < SMALL_WORDS * 4; ++j)
-        if ((uint32_t)j < len) sfa_step<false>(ch, reg_byte(w, j), j, R, s_cls, T.nc, nr, T.ncls, A);
+        for (uint32_t b = 0; b < 4; ++b) {
+            const uint32_t j = 4 * k + b;
+            if (j >= jlo && j < jhi) sfa_step<false>(ch, (x >> (8 * b)) & 0xffu, (int32_t)j, R, s_cls, T.nc, nr, T.ncls, A);
+        }
+    }
     uint32_t ps = NO_POINT;
     if (ch.f & NC_POINT) {
         ps = point_source_of<false>(ch.f);
@@ -136,12 +148,15 @@ __global__ void __launch_bounds__(SMALL_THREADS) sfa_small_kernel(Tables T, cons
     if (cm) {
         const int lc = 31 - __clz(cm);
         uint32_t v = __shfl_sync(0xffffffffu, fl, lc);
+#pragma unroll 1
         for (int i = lc + 1; i < 32; ++i) v = amap(__shfl_sync(0xffffffffu, fl, i), v);
         if (lane == 0) s_gval[warp] = v;
     } else {
+#pragma unroll 1
         for (uint32_t qb = 0; qb < nr; qb += 32) {
             const uint32_t q = qb + lane;
             uint32_t v = q < nr ? q : 0u;
+#pragma unroll 1
             for (int i = 0; i < 32; ++i) v = amap(__shfl_sync(0xffffffffu, fl, i), v);
             if (q < nr) s_gvec[(size_t)warp * nr + q] = (uint8_t)v;
         }
@@ -165,6 +180,7 @@ __global__ void __launch_bounds__(SMALL_THREADS) sfa_small_kernel(Tables T, cons
     // below it, then the vector groups in between
     if (warp == 0 && lane < G) {
         uint32_t below = 0;
+#pragma unroll 1
         for (int g = 0; g < lane; ++g)
             if (s_gval[g] != 0xffffffffu) below |= 1u << g;
         int j;
@@ -176,25 +192,33 @@ __global__ void __launch_bounds__(SMALL_THREADS) sfa_small_kernel(Tables T, cons
             j = -1;
             v = s_misc[0];
         }
+#pragma unroll 1
         for (int g = j + 1; g < lane; ++g) v = s_gvec[(size_t)g * nr + v];
         s_gpre[lane] = v;
     }
     __syncthreads();
 
-    // entering state of this chunk, pass 2 from the registers, the state after it
+    // entering state of this chunk, pass 2 from shared memory, the state after it
     const uint32_t below = cm & lanemask_lt;
     const int jc = below ? 31 - __clz(below) : -1;
     uint32_t v = __shfl_sync(0xffffffffu, fl, jc < 0 ? 0 : jc);
     if (jc < 0) v = s_gpre[warp];
+#pragma unroll 1
     for (int i = jc + 1; i < lane; ++i) v = amap(s_f[warp * 32 + i], v);
     unsigned long long cnt = ch.cnt;
     if (ch.lm >= 0) {
+        const uint32_t lm = (uint32_t)ch.lm;
         uint32_t q = v, c = 0;
+#pragma unroll 1
+        for (uint32_t k = jlo >> 2; 4 * k <= lm; ++k) {
+            const uint32_t x = s_txt[k * SMALL_THREADS + tid];
 #pragma unroll
-        for (int j = 0; j < SMALL_WORDS * 4; ++j) {
-            if (j <= ch.lm) {
-                q = R.next(q, reg_byte(w, j));
-                c += q >= A;
+            for (uint32_t b = 0; b < 4; ++b) {
+                const uint32_t j = 4 * k + b;
+                if (j >= jlo && j <= lm) {
+                    q = R.next(q, (x >> (8 * b)) & 0xffu);
+                    c += q >= A;
+                }
             }
         }
         cnt = c + chunk_count_after(ch, v, ps, T);
@@ -206,6 +230,7 @@ __global__ void __launch_bounds__(SMALL_THREADS) sfa_small_kernel(Tables T, cons
     __syncthreads();
     if (tid == 0) {
         unsigned long long total = 0;
+#pragma unroll 1
         for (int g = 0; g < G; ++g) total += s_red[g];
         const uint32_t fin = s_misc[2];
         sfa_result r;
