@@ -138,8 +138,10 @@ const uint8_t *device_readable(const uint8_t *h);
 
 // kernels_small.cu: the short-text kernel (one CTA, no scratch, no look-back)
 bool small_fits(uint64_t n);
-int launch_small(const sfa_dev::Tables &T, const uint8_t *text, uint64_t n, bool carry, sfa_result *out,
-                 cudaStream_t s);
+// n_nc: the handle's stored non-constant rows (staged in shared memory when
+// they fit)
+int launch_small(const sfa_dev::Tables &T, uint64_t n_nc, const uint8_t *text, uint64_t n, bool carry,
+                 sfa_result *out, cudaStream_t s);
 
 // regex.cpp
 int regex_to_dfa(const char *pattern, size_t len, uint32_t flags, int32_t cap, std::vector<int32_t> &delta,

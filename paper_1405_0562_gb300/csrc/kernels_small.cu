@@ -7,8 +7,12 @@
 // recounts the prefix whose acceptance depended on the entering state.  D-SFA
 // handles with byte state ids only.  Every loop over text bytes is rolled: a
 // launch of a few microseconds lands on an SM whose instruction cache does
-// not hold this kernel, so its code is kept short.
+// not hold this kernel, so its code is kept short.  The launch's latency is
+// a chain of dependent loads, so every global load of the set-up is issued
+// before the first shared-memory store, and the non-constant rows are staged
+// in shared memory when they fit (pass 1 then never waits on L2).
 #include <algorithm>
+#include <atomic>
 
 #include "api_internal.h"
 #include "sfa_device.cuh"
@@ -30,12 +34,43 @@ struct SmallLayout {
     static SFA_HD size_t misc_off(uint32_t nr) { return red_off(nr) + G * 8; }
     static SFA_HD size_t txt_off(uint32_t nr) { return misc_off(nr) + 16; }
     static SFA_HD size_t gvec_off(uint32_t nr) { return txt_off(nr) + (size_t)SMALL_WORDS * SMALL_THREADS * 4; }
-    static SFA_HD size_t bytes(uint32_t nr) { return a16(gvec_off(nr) + (size_t)G * nr); }
+    static SFA_HD size_t nc_off(uint32_t nr) { return a16(gvec_off(nr) + (size_t)G * nr); }
+    static SFA_HD size_t bytes(uint32_t nr) { return nc_off(nr); }
+    // with the non-constant rows (nc_words 32-bit entries) staged
+    static SFA_HD size_t bytes(uint32_t nr, uint64_t nc_words) { return a16(nc_off(nr) + nc_words * 4); }
 };
+
+constexpr uint32_t GV_IDENT = 0xfffffffeu;    // a group of f_I chunks (past the text)
+constexpr uint32_t GV_VEC = 0xffffffffu;      // a group summarised by a |Q|-vector
+
+// sfa_step over byte ids with a generic load of the non-constant row entry:
+// the rows are in shared memory or in global memory
+__device__ __forceinline__ void small_step(Chain &s, uint32_t b, int32_t j, const Rows<false> &R,
+                                           const uint8_t *s_cls, const uint32_t *nc, uint32_t nr, uint32_t ncls,
+                                           uint32_t first_accept) {
+    using P = Pt<false>;
+    if (s.f & NC_POINT) {
+        const uint32_t p = R.next(s.f & P::MASK, b);
+        s.cnt += p >= first_accept;
+        s.f = (s.f & ~P::MASK) | p;
+    } else if (s.f >= nr) {
+        const uint32_t e = nc[(size_t)(s.f - nr) * ncls + s_cls[b]];
+        const uint32_t a = e >> 30;
+        const bool pt = (e & NC_POINT) != 0u;
+        const bool mark = a == ACC_MIXED || pt;
+        s.f = e & (pt ? P::KEEP : NC_ID_MASK);
+        s.cnt += a == ACC_ALL;
+        s.lm = mark ? j : s.lm;
+        s.snap = mark ? s.cnt : s.snap;
+    } else {
+        s.f = R.next(s.f, b);
+        s.cnt += s.f >= first_accept;
+    }
+}
 
 __global__ void __launch_bounds__(SMALL_THREADS) sfa_small_kernel(Tables T, const uint8_t *text, uint64_t n,
                                                                   uint32_t chunk, uint32_t origin, uint32_t carry,
-                                                                  sfa_result *out) {
+                                                                  uint32_t nc_words, sfa_result *out) {
     using L = SmallLayout;
     constexpr int G = L::G;
     extern __shared__ __align__(128) uint8_t smem[];
@@ -49,6 +84,7 @@ __global__ void __launch_bounds__(SMALL_THREADS) sfa_small_kernel(Tables T, cons
     uint32_t *s_misc = reinterpret_cast<uint32_t *>(smem + L::misc_off(nr));
     uint32_t *s_txt = reinterpret_cast<uint32_t *>(smem + L::txt_off(nr));
     uint8_t *s_gvec = smem + L::gvec_off(nr);
+    uint32_t *s_nc = reinterpret_cast<uint32_t *>(smem + L::nc_off(nr));
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t lanemask_lt = (1u << lane) - 1u;
     Rows<false> R;
@@ -65,54 +101,75 @@ __global__ void __launch_bounds__(SMALL_THREADS) sfa_small_kernel(Tables T, cons
     const uint64_t ve = ve_c < ve_t ? ve_c : ve_t;
     const uint32_t jlo = tid == 0 ? head : 0u;
     const uint32_t jhi = ve > vs ? (uint32_t)(ve - vs) : 0u;
+    // every global load first: two 16-byte units of DFA rows per thread, the
+    // chunk's full 16-byte units, the class table
+    const uint4 *dsrc = reinterpret_cast<const uint4 *>(T.dfa);
+    const uint32_t n16 = nr * 16;
+    uint4 dv[2];
+#pragma unroll
+    for (uint32_t u = 0; u < 2; ++u) {
+        const uint32_t i = u * SMALL_THREADS + tid;
+        if (i < n16) dv[u] = __ldg(dsrc + i);
+    }
+    uint4 tx[SMALL_WORDS / 4];
 #pragma unroll
     for (uint32_t u = 0; u < (uint32_t)SMALL_WORDS / 4; ++u) {
         const uint32_t a = 16 * u;
-        uint4 x = make_uint4(0, 0, 0, 0);
-        if (jlo <= a && a + 16 <= jhi) {
-            x = ldg128(text + (vs + a - head));
-        } else if (a < jhi && a + 16 > jlo) {   // the text's first or last partial 16 bytes
+        tx[u] = make_uint4(0, 0, 0, 0);
+        if (jlo <= a && a + 16 <= jhi) tx[u] = ldg128(text + (vs + a - head));
+    }
+    uint4 cv = make_uint4(0, 0, 0, 0);
+    if (tid < 16) cv = __ldg(reinterpret_cast<const uint4 *>(T.cls) + tid);
+    // the text's first or last partial 16 bytes (chunk 0 and the last chunk)
+#pragma unroll 1
+    for (uint32_t u = 0; u < (uint32_t)SMALL_WORDS / 4; ++u) {
+        const uint32_t a = 16 * u;
+        if (!(jlo <= a && a + 16 <= jhi) && a < jhi && a + 16 > jlo) {
             uint32_t wd[4] = {0, 0, 0, 0};
 #pragma unroll
             for (uint32_t b = 0; b < 16; ++b)
                 if (a + b >= jlo && a + b < jhi) wd[b >> 2] |= (uint32_t)__ldg(text + (vs + a + b - head)) << (8 * (b & 3));
-            x = make_uint4(wd[0], wd[1], wd[2], wd[3]);
-        }
-        if (a < jhi) {
-            s_txt[(4 * u + 0) * SMALL_THREADS + tid] = x.x;
-            s_txt[(4 * u + 1) * SMALL_THREADS + tid] = x.y;
-            s_txt[(4 * u + 2) * SMALL_THREADS + tid] = x.z;
-            s_txt[(4 * u + 3) * SMALL_THREADS + tid] = x.w;
+            s_txt[(4 * u + 0) * SMALL_THREADS + tid] = wd[0];
+            s_txt[(4 * u + 1) * SMALL_THREADS + tid] = wd[1];
+            s_txt[(4 * u + 2) * SMALL_THREADS + tid] = wd[2];
+            s_txt[(4 * u + 3) * SMALL_THREADS + tid] = wd[3];
         }
     }
-    // the DFA rows (ROWB apart) and the class table, every load in flight
-    {
-        const uint4 *src = reinterpret_cast<const uint4 *>(T.dfa);
-        const uint32_t n16 = nr * 16;
-        uint4 v[2];
 #pragma unroll
-        for (uint32_t u = 0; u < 2; ++u) {
-            const uint32_t i = u * SMALL_THREADS + tid;
-            if (i < n16) v[u] = __ldg(src + i);
+    for (uint32_t u = 0; u < (uint32_t)SMALL_WORDS / 4; ++u) {
+        const uint32_t a = 16 * u;
+        if (jlo <= a && a + 16 <= jhi) {
+            s_txt[(4 * u + 0) * SMALL_THREADS + tid] = tx[u].x;
+            s_txt[(4 * u + 1) * SMALL_THREADS + tid] = tx[u].y;
+            s_txt[(4 * u + 2) * SMALL_THREADS + tid] = tx[u].z;
+            s_txt[(4 * u + 3) * SMALL_THREADS + tid] = tx[u].w;
         }
-#pragma unroll 1
-        for (uint32_t i = 2 * SMALL_THREADS + tid; i < n16; i += SMALL_THREADS) {
-            const uint4 x = __ldg(src + i);
+    }
+#pragma unroll
+    for (uint32_t u = 0; u < 2; ++u) {
+        const uint32_t i = u * SMALL_THREADS + tid;
+        if (i < n16) {
             uint2 *dst = reinterpret_cast<uint2 *>(s_dfa + (i >> 4) * ROWB + (i & 15) * 16);
-            dst[0] = make_uint2(x.x, x.y);
-            dst[1] = make_uint2(x.z, x.w);
+            dst[0] = make_uint2(dv[u].x, dv[u].y);
+            dst[1] = make_uint2(dv[u].z, dv[u].w);
         }
-#pragma unroll
-        for (uint32_t u = 0; u < 2; ++u) {
-            const uint32_t i = u * SMALL_THREADS + tid;
-            if (i < n16) {
-                uint2 *dst = reinterpret_cast<uint2 *>(s_dfa + (i >> 4) * ROWB + (i & 15) * 16);
-                dst[0] = make_uint2(v[u].x, v[u].y);
-                dst[1] = make_uint2(v[u].z, v[u].w);
-            }
-        }
-        if (tid < 16) reinterpret_cast<uint4 *>(s_cls)[tid] = __ldg(reinterpret_cast<const uint4 *>(T.cls) + tid);
     }
+    if (tid < 16) reinterpret_cast<uint4 *>(s_cls)[tid] = cv;
+    // DFA rows past the first 128, then the non-constant rows (the table's
+    // region is 256-byte aligned and padded: whole 16-byte units are read)
+#pragma unroll 1
+    for (uint32_t i = 2 * SMALL_THREADS + tid; i < n16; i += SMALL_THREADS) {
+        const uint4 x = __ldg(dsrc + i);
+        uint2 *dst = reinterpret_cast<uint2 *>(s_dfa + (i >> 4) * ROWB + (i & 15) * 16);
+        dst[0] = make_uint2(x.x, x.y);
+        dst[1] = make_uint2(x.z, x.w);
+    }
+    const uint32_t nc16 = (nc_words + 3) / 4;
+    const uint4 *nsrc = reinterpret_cast<const uint4 *>(T.nc);
+    uint4 *ndst = reinterpret_cast<uint4 *>(s_nc);
+#pragma unroll 4
+    for (uint32_t i = tid; i < nc16; i += SMALL_THREADS) ndst[i] = __ldg(nsrc + i);
+    const uint32_t *ncp = nc_words ? s_nc : T.nc;
     __syncthreads();
 
     // pass 1: the chunk from f_I, one word (4 bytes) per iteration
@@ -128,7 +185,7 @@ __global__ void __launch_bounds__(SMALL_THREADS) sfa_small_kernel(Tables T, cons
 #pragma unroll
         for (uint32_t b = 0; b < 4; ++b) {
             const uint32_t j = 4 * k + b;
-            if (j >= jlo && j < jhi) sfa_step<false>(ch, (x >> (8 * b)) & 0xffu, (int32_t)j, R, s_cls, T.nc, nr, T.ncls, A);
+            if (j >= jlo && j < jhi) small_step(ch, (x >> (8 * b)) & 0xffu, (int32_t)j, R, s_cls, ncp, nr, T.ncls, A);
         }
     }
     uint32_t ps = NO_POINT;
@@ -140,27 +197,39 @@ __global__ void __launch_bounds__(SMALL_THREADS) sfa_small_kernel(Tables T, cons
     const uint32_t fl = ch.f;
     s_f[tid] = fl;
 
-    // group (warp) summaries: a constant, or a |Q|-vector with lanes over states
-    // (the chunks of threads past the end of the text are f_I, which every
-    // composition below skips)
+    // group (warp) summaries: a constant, f_I (every chunk past the text), or
+    // a |Q|-vector with lanes over states; compositions skip f_I chunks
     auto amap = [&](uint32_t f, uint32_t v) -> uint32_t { return f == T.ident ? v : apply_map(f, v, T.maps, nr); };
+    const uint32_t am = __ballot_sync(0xffffffffu, fl != T.ident);
     const uint32_t cm = __ballot_sync(0xffffffffu, fl < nr);
     if (cm) {
         const int lc = 31 - __clz(cm);
         uint32_t v = __shfl_sync(0xffffffffu, fl, lc);
+        uint32_t m = am & ~((2u << lc) - 1u);
 #pragma unroll 1
-        for (int i = lc + 1; i < 32; ++i) v = amap(__shfl_sync(0xffffffffu, fl, i), v);
+        while (m) {
+            const int i = __ffs(m) - 1;
+            m &= m - 1u;
+            v = apply_map(__shfl_sync(0xffffffffu, fl, i), v, T.maps, nr);
+        }
         if (lane == 0) s_gval[warp] = v;
+    } else if (!am) {
+        if (lane == 0) s_gval[warp] = GV_IDENT;
     } else {
 #pragma unroll 1
         for (uint32_t qb = 0; qb < nr; qb += 32) {
             const uint32_t q = qb + lane;
             uint32_t v = q < nr ? q : 0u;
+            uint32_t m = am;
 #pragma unroll 1
-            for (int i = 0; i < 32; ++i) v = amap(__shfl_sync(0xffffffffu, fl, i), v);
+            while (m) {
+                const int i = __ffs(m) - 1;
+                m &= m - 1u;
+                v = apply_map(__shfl_sync(0xffffffffu, fl, i), v, T.maps, nr);
+            }
             if (q < nr) s_gvec[(size_t)warp * nr + q] = (uint8_t)v;
         }
-        if (lane == 0) s_gval[warp] = 0xffffffffu;   // marks a vector group
+        if (lane == 0) s_gval[warp] = GV_VEC;
     }
     // the entering state of the text: q0, or the carried result's state
     if (tid == 0) {
@@ -182,7 +251,7 @@ __global__ void __launch_bounds__(SMALL_THREADS) sfa_small_kernel(Tables T, cons
         uint32_t below = 0;
 #pragma unroll 1
         for (int g = 0; g < lane; ++g)
-            if (s_gval[g] != 0xffffffffu) below |= 1u << g;
+            if (s_gval[g] < GV_IDENT) below |= 1u << g;
         int j;
         uint32_t v;
         if (below) {
@@ -193,7 +262,8 @@ __global__ void __launch_bounds__(SMALL_THREADS) sfa_small_kernel(Tables T, cons
             v = s_misc[0];
         }
 #pragma unroll 1
-        for (int g = j + 1; g < lane; ++g) v = s_gvec[(size_t)g * nr + v];
+        for (int g = j + 1; g < lane; ++g)
+            if (s_gval[g] == GV_VEC) v = s_gvec[(size_t)g * nr + v];
         s_gpre[lane] = v;
     }
     __syncthreads();
@@ -203,8 +273,13 @@ __global__ void __launch_bounds__(SMALL_THREADS) sfa_small_kernel(Tables T, cons
     const int jc = below ? 31 - __clz(below) : -1;
     uint32_t v = __shfl_sync(0xffffffffu, fl, jc < 0 ? 0 : jc);
     if (jc < 0) v = s_gpre[warp];
+    uint32_t mb = am & lanemask_lt & (jc < 0 ? 0xffffffffu : ~((2u << jc) - 1u));
 #pragma unroll 1
-    for (int i = jc + 1; i < lane; ++i) v = amap(s_f[warp * 32 + i], v);
+    while (mb) {
+        const int i = __ffs(mb) - 1;
+        mb &= mb - 1u;
+        v = apply_map(s_f[warp * 32 + i], v, T.maps, nr);
+    }
     unsigned long long cnt = ch.cnt;
     if (ch.lm >= 0) {
         const uint32_t lm = (uint32_t)ch.lm;
@@ -251,8 +326,8 @@ bool small_fits(uint64_t n) { return n <= (uint64_t)sfa_dev::SMALL_THREADS * sfa
 
 size_t small_smem(uint32_t nr) { return sfa_dev::SmallLayout::bytes(nr); }
 
-int launch_small(const sfa_dev::Tables &T, const uint8_t *text, uint64_t n, bool carry, sfa_result *out,
-                 cudaStream_t s) {
+int launch_small(const sfa_dev::Tables &T, uint64_t n_nc, const uint8_t *text, uint64_t n, bool carry,
+                 sfa_result *out, cudaStream_t s) {
     if (!small_fits(n) || T.nr > 255) return SFA_ERR_UNSUPPORTED;
     // chunk bodies from the first 16-byte boundary, in 16-byte multiples
     const uint32_t origin = n ? sfa_dev::text_origin(text) : 0u;
@@ -260,16 +335,23 @@ int launch_small(const sfa_dev::Tables &T, const uint8_t *text, uint64_t n, bool
     uint32_t chunk = (uint32_t)((body + sfa_dev::SMALL_THREADS - 1) / sfa_dev::SMALL_THREADS);
     chunk = std::max<uint32_t>(16, (chunk + 15) & ~15u);
     if (chunk > (uint32_t)sfa_dev::SMALL_CHUNK) return SFA_ERR_UNSUPPORTED;
-    static const bool attr = [] {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        return cudaFuncSetAttribute(reinterpret_cast<const void *>(&sfa_dev::sfa_small_kernel),
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)device_props(dev).smem_optin) == cudaSuccess;
-    }();
-    if (!attr) return SFA_ERR_CUDA;
-    const size_t smem = small_smem(T.nr);
-    sfa_dev::sfa_small_kernel<<<1, sfa_dev::SMALL_THREADS, smem, s>>>(T, text, n, chunk, origin, carry ? 1u : 0u, out);
+    // the kernel's shared-memory limit, raised once per device
+    static std::atomic<uint8_t> attr_done[64];
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    const size_t optin = device_props(dev).smem_optin;
+    if (dev < 0 || dev >= 64) return SFA_ERR_UNSUPPORTED;
+    if (!attr_done[dev].load(std::memory_order_acquire)) {
+        CK(cudaFuncSetAttribute(reinterpret_cast<const void *>(&sfa_dev::sfa_small_kernel),
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)optin));
+        attr_done[dev].store(1, std::memory_order_release);
+    }
+    // the non-constant rows go to shared memory when they fit
+    const uint64_t nc_words = n_nc * T.ncls;
+    const bool stage = nc_words && sfa_dev::SmallLayout::bytes(T.nr, nc_words) <= optin;
+    const size_t smem = stage ? sfa_dev::SmallLayout::bytes(T.nr, nc_words) : small_smem(T.nr);
+    sfa_dev::sfa_small_kernel<<<1, sfa_dev::SMALL_THREADS, smem, s>>>(T, text, n, chunk, origin, carry ? 1u : 0u,
+                                                                     stage ? (uint32_t)nc_words : 0u, out);
     CK(cudaGetLastError());
     g_launches.fetch_add(1, std::memory_order_relaxed);
     return SFA_OK;

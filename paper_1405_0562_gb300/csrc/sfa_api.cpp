@@ -492,7 +492,7 @@ int match_impl(sfa_handle *h, const uint8_t *d_text, uint64_t n, sfa_result *d_o
                                    o->forced_chunks || o->debug_flags || o->tiling);
     if (!d_map && !shape_given && h->host.mode == SFA_MODE_SFA && !h->host.wide && h->host.nr <= 255 &&
         small_fits(n))
-        return launch_small(h->dev, d_text, n, carry, d_out, s);
+        return launch_small(h->dev, h->host.n_nc, d_text, n, carry, d_out, s);
     Shape sh;
     int rc = choose_shape(h, n, o, sh);
     if (rc) return rc;
