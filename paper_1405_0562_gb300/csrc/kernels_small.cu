@@ -8,9 +8,11 @@
 // handles with byte state ids only.  Every loop over text bytes is rolled: a
 // launch of a few microseconds lands on an SM whose instruction cache does
 // not hold this kernel, so its code is kept short.  The launch's latency is
-// a chain of dependent loads, so every global load of the set-up is issued
-// before the first shared-memory store, and the non-constant rows are staged
-// in shared memory when they fit (pass 1 then never waits on L2).
+// a chain of dependent loads, so the tables arrive by asynchronous copies
+// issued together with the text's loads (one wait for all of them), the
+// non-constant rows are staged in shared memory when they fit (pass 1 then
+// never waits on L2), and the scans and the final sum use warp ballots and
+// shuffles instead of loops over shared memory.
 #include <algorithm>
 #include <atomic>
 
@@ -34,27 +36,43 @@ struct SmallLayout {
     static SFA_HD size_t misc_off(uint32_t nr) { return red_off(nr) + G * 8; }
     static SFA_HD size_t txt_off(uint32_t nr) { return misc_off(nr) + 16; }
     static SFA_HD size_t gvec_off(uint32_t nr) { return txt_off(nr) + (size_t)SMALL_WORDS * SMALL_THREADS * 4; }
-    static SFA_HD size_t nc_off(uint32_t nr) { return a16(gvec_off(nr) + (size_t)G * nr); }
+    static SFA_HD size_t orig_off(uint32_t nr) { return a16(gvec_off(nr) + (size_t)G * nr); }
+    static SFA_HD size_t nc_off(uint32_t nr) { return a16(orig_off(nr) + (size_t)nr * 4); }
     static SFA_HD size_t bytes(uint32_t nr) { return nc_off(nr); }
     // with the non-constant rows (nc_words 32-bit entries) staged
     static SFA_HD size_t bytes(uint32_t nr, uint64_t nc_words) { return a16(nc_off(nr) + nc_words * 4); }
 };
+static_assert(SmallLayout::G == 32, "the group scans are one warp wide");
 
 constexpr uint32_t GV_IDENT = 0xfffffffeu;    // a group of f_I chunks (past the text)
 constexpr uint32_t GV_VEC = 0xffffffffu;      // a group summarised by a |Q|-vector
 
-// sfa_step over byte ids with a generic load of the non-constant row entry:
-// the rows are in shared memory or in global memory
-__device__ __forceinline__ void small_step(Chain &s, uint32_t b, int32_t j, const Rows<false> &R,
-                                           const uint8_t *s_cls, const uint32_t *nc, uint32_t nr, uint32_t ncls,
-                                           uint32_t first_accept) {
+// asynchronous global -> shared copies (no register holds the data)
+__device__ __forceinline__ void cp_async4(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// byte b of a text word
+__device__ __forceinline__ uint32_t wbyte(uint32_t x, uint32_t b) { return __byte_perm(x, 0, 0x4440 | b); }
+
+// sfa_step over byte ids, given the byte's class, with a generic load of the
+// non-constant row entry (the rows are in shared or in global memory)
+__device__ __forceinline__ void small_step(Chain &s, uint32_t b, uint32_t cl, int32_t j, const Rows<false> &R,
+                                           const uint32_t *nc, uint32_t nr, uint32_t ncls, uint32_t first_accept) {
     using P = Pt<false>;
     if (s.f & NC_POINT) {
         const uint32_t p = R.next(s.f & P::MASK, b);
         s.cnt += p >= first_accept;
         s.f = (s.f & ~P::MASK) | p;
     } else if (s.f >= nr) {
-        const uint32_t e = nc[(size_t)(s.f - nr) * ncls + s_cls[b]];
+        const uint32_t e = nc[(size_t)(s.f - nr) * ncls + cl];
         const uint32_t a = e >> 30;
         const bool pt = (e & NC_POINT) != 0u;
         const bool mark = a == ACC_MIXED || pt;
@@ -68,7 +86,7 @@ __device__ __forceinline__ void small_step(Chain &s, uint32_t b, int32_t j, cons
     }
 }
 
-__global__ void __launch_bounds__(SMALL_THREADS) sfa_small_kernel(Tables T, const uint8_t *text, uint64_t n,
+__global__ void __launch_bounds__(SMALL_THREADS, 1) sfa_small_kernel(Tables T, const uint8_t *text, uint64_t n,
                                                                   uint32_t chunk, uint32_t origin, uint32_t carry,
                                                                   uint32_t nc_words, sfa_result *out) {
     using L = SmallLayout;
@@ -84,6 +102,7 @@ __global__ void __launch_bounds__(SMALL_THREADS) sfa_small_kernel(Tables T, cons
     uint32_t *s_misc = reinterpret_cast<uint32_t *>(smem + L::misc_off(nr));
     uint32_t *s_txt = reinterpret_cast<uint32_t *>(smem + L::txt_off(nr));
     uint8_t *s_gvec = smem + L::gvec_off(nr);
+    int32_t *s_orig = reinterpret_cast<int32_t *>(smem + L::orig_off(nr));
     uint32_t *s_nc = reinterpret_cast<uint32_t *>(smem + L::nc_off(nr));
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t lanemask_lt = (1u << lane) - 1u;
@@ -101,16 +120,8 @@ __global__ void __launch_bounds__(SMALL_THREADS) sfa_small_kernel(Tables T, cons
     const uint64_t ve = ve_c < ve_t ? ve_c : ve_t;
     const uint32_t jlo = tid == 0 ? head : 0u;
     const uint32_t jhi = ve > vs ? (uint32_t)(ve - vs) : 0u;
-    // every global load first: two 16-byte units of DFA rows per thread, the
-    // chunk's full 16-byte units, the class table
-    const uint4 *dsrc = reinterpret_cast<const uint4 *>(T.dfa);
-    const uint32_t n16 = nr * 16;
-    uint4 dv[2];
-#pragma unroll
-    for (uint32_t u = 0; u < 2; ++u) {
-        const uint32_t i = u * SMALL_THREADS + tid;
-        if (i < n16) dv[u] = __ldg(dsrc + i);
-    }
+
+    // the chunk's full 16-byte units into registers
     uint4 tx[SMALL_WORDS / 4];
 #pragma unroll
     for (uint32_t u = 0; u < (uint32_t)SMALL_WORDS / 4; ++u) {
@@ -118,8 +129,19 @@ __global__ void __launch_bounds__(SMALL_THREADS) sfa_small_kernel(Tables T, cons
         tx[u] = make_uint4(0, 0, 0, 0);
         if (jlo <= a && a + 16 <= jhi) tx[u] = ldg128(text + (vs + a - head));
     }
-    uint4 cv = make_uint4(0, 0, 0, 0);
-    if (tid < 16) cv = __ldg(reinterpret_cast<const uint4 *>(T.cls) + tid);
+    // the tables by asynchronous copies: DFA rows in 8-byte pieces (rows ROWB
+    // apart), the class table, the caller's state ids, the non-constant rows
+    // when staged (their region is 256-byte aligned and padded: whole 16-byte
+    // units are read)
+#pragma unroll 1
+    for (uint32_t i = tid; i < nr * 32; i += SMALL_THREADS)
+        cp_async8(s_dfa + (i >> 5) * ROWB + (i & 31) * 8, T.dfa + (size_t)i * 8);
+    if (tid < 16) cp_async16(s_cls + tid * 16, T.cls + tid * 16);
+    if ((uint32_t)tid < nr) cp_async4(s_orig + tid, T.orig_of + tid);
+    const uint32_t nc16 = (nc_words + 3) / 4;
+#pragma unroll 1
+    for (uint32_t i = tid; i < nc16; i += SMALL_THREADS) cp_async16(s_nc + 4 * i, T.nc + 4 * i);
+    const uint32_t *ncp = nc_words ? s_nc : T.nc;
     // the text's first or last partial 16 bytes (chunk 0 and the last chunk)
 #pragma unroll 1
     for (uint32_t u = 0; u < (uint32_t)SMALL_WORDS / 4; ++u) {
@@ -145,34 +167,11 @@ __global__ void __launch_bounds__(SMALL_THREADS) sfa_small_kernel(Tables T, cons
             s_txt[(4 * u + 3) * SMALL_THREADS + tid] = tx[u].w;
         }
     }
-#pragma unroll
-    for (uint32_t u = 0; u < 2; ++u) {
-        const uint32_t i = u * SMALL_THREADS + tid;
-        if (i < n16) {
-            uint2 *dst = reinterpret_cast<uint2 *>(s_dfa + (i >> 4) * ROWB + (i & 15) * 16);
-            dst[0] = make_uint2(dv[u].x, dv[u].y);
-            dst[1] = make_uint2(dv[u].z, dv[u].w);
-        }
-    }
-    if (tid < 16) reinterpret_cast<uint4 *>(s_cls)[tid] = cv;
-    // DFA rows past the first 128, then the non-constant rows (the table's
-    // region is 256-byte aligned and padded: whole 16-byte units are read)
-#pragma unroll 1
-    for (uint32_t i = 2 * SMALL_THREADS + tid; i < n16; i += SMALL_THREADS) {
-        const uint4 x = __ldg(dsrc + i);
-        uint2 *dst = reinterpret_cast<uint2 *>(s_dfa + (i >> 4) * ROWB + (i & 15) * 16);
-        dst[0] = make_uint2(x.x, x.y);
-        dst[1] = make_uint2(x.z, x.w);
-    }
-    const uint32_t nc16 = (nc_words + 3) / 4;
-    const uint4 *nsrc = reinterpret_cast<const uint4 *>(T.nc);
-    uint4 *ndst = reinterpret_cast<uint4 *>(s_nc);
-#pragma unroll 4
-    for (uint32_t i = tid; i < nc16; i += SMALL_THREADS) ndst[i] = __ldg(nsrc + i);
-    const uint32_t *ncp = nc_words ? s_nc : T.nc;
+    cp_async_wait_all();
     __syncthreads();
 
-    // pass 1: the chunk from f_I, one word (4 bytes) per iteration
+    // pass 1: the chunk from f_I, one word (4 bytes) per iteration; a word
+    // entered with a constant mapping is four DFA-row lookups
     Chain ch;
     ch.f = T.ident;
     ch.cnt = 0;
@@ -182,10 +181,25 @@ __global__ void __launch_bounds__(SMALL_THREADS) sfa_small_kernel(Tables T, cons
 #pragma unroll 1
     for (uint32_t k = jlo >> 2; k < kend; ++k) {
         const uint32_t x = s_txt[k * SMALL_THREADS + tid];
+        const uint32_t j0 = 4 * k;
+        if (j0 >= jlo && j0 + 4 <= jhi && ch.f < nr) {
+            uint32_t q = ch.f, c = 0;
 #pragma unroll
-        for (uint32_t b = 0; b < 4; ++b) {
-            const uint32_t j = 4 * k + b;
-            if (j >= jlo && j < jhi) small_step(ch, (x >> (8 * b)) & 0xffu, (int32_t)j, R, s_cls, ncp, nr, T.ncls, A);
+            for (uint32_t b = 0; b < 4; ++b) {
+                q = R.next(q, wbyte(x, b));
+                c += q >= A;
+            }
+            ch.f = q;
+            ch.cnt += c;
+        } else {
+            uint32_t cl[4];
+#pragma unroll
+            for (uint32_t b = 0; b < 4; ++b) cl[b] = s_cls[wbyte(x, b)];
+#pragma unroll
+            for (uint32_t b = 0; b < 4; ++b) {
+                const uint32_t j = j0 + b;
+                if (j >= jlo && j < jhi) small_step(ch, wbyte(x, b), cl[b], (int32_t)j, R, ncp, nr, T.ncls, A);
+            }
         }
     }
     uint32_t ps = NO_POINT;
@@ -199,7 +213,6 @@ __global__ void __launch_bounds__(SMALL_THREADS) sfa_small_kernel(Tables T, cons
 
     // group (warp) summaries: a constant, f_I (every chunk past the text), or
     // a |Q|-vector with lanes over states; compositions skip f_I chunks
-    auto amap = [&](uint32_t f, uint32_t v) -> uint32_t { return f == T.ident ? v : apply_map(f, v, T.maps, nr); };
     const uint32_t am = __ballot_sync(0xffffffffu, fl != T.ident);
     const uint32_t cm = __ballot_sync(0xffffffffu, fl < nr);
     if (cm) {
@@ -245,25 +258,23 @@ __global__ void __launch_bounds__(SMALL_THREADS) sfa_small_kernel(Tables T, cons
         s_misc[1] = bad;
     }
     __syncthreads();
-    // exclusive prefix of every group (warp 0): the nearest constant group
-    // below it, then the vector groups in between
-    if (warp == 0 && lane < G) {
-        uint32_t below = 0;
+    // exclusive prefix of every group (warp 0, lane g for group g): the
+    // nearest constant group below it, then the vector groups in between
+    if (warp == 0) {
+        const uint32_t gv = s_gval[lane];
+        const uint32_t cgm = __ballot_sync(0xffffffffu, gv < GV_IDENT);
+        const uint32_t vgm = __ballot_sync(0xffffffffu, gv == GV_VEC);
+        const uint32_t below = cgm & lanemask_lt;
+        const int j = below ? 31 - __clz(below) : -1;
+        const uint32_t vj = __shfl_sync(0xffffffffu, gv, j < 0 ? 0 : j);
+        uint32_t v = j < 0 ? s_misc[0] : vj;
+        uint32_t m = vgm & lanemask_lt & (j < 0 ? 0xffffffffu : ~((2u << j) - 1u));
 #pragma unroll 1
-        for (int g = 0; g < lane; ++g)
-            if (s_gval[g] < GV_IDENT) below |= 1u << g;
-        int j;
-        uint32_t v;
-        if (below) {
-            j = 31 - __clz(below);
-            v = s_gval[j];
-        } else {
-            j = -1;
-            v = s_misc[0];
+        while (m) {
+            const int g = __ffs(m) - 1;
+            m &= m - 1u;
+            v = s_gvec[(size_t)g * nr + v];
         }
-#pragma unroll 1
-        for (int g = j + 1; g < lane; ++g)
-            if (s_gval[g] == GV_VEC) v = s_gvec[(size_t)g * nr + v];
         s_gpre[lane] = v;
     }
     __syncthreads();
@@ -287,34 +298,45 @@ __global__ void __launch_bounds__(SMALL_THREADS) sfa_small_kernel(Tables T, cons
 #pragma unroll 1
         for (uint32_t k = jlo >> 2; 4 * k <= lm; ++k) {
             const uint32_t x = s_txt[k * SMALL_THREADS + tid];
+            const uint32_t j0 = 4 * k;
+            if (j0 >= jlo && j0 + 3 <= lm) {
 #pragma unroll
-            for (uint32_t b = 0; b < 4; ++b) {
-                const uint32_t j = 4 * k + b;
-                if (j >= jlo && j <= lm) {
-                    q = R.next(q, (x >> (8 * b)) & 0xffu);
+                for (uint32_t b = 0; b < 4; ++b) {
+                    q = R.next(q, wbyte(x, b));
                     c += q >= A;
+                }
+            } else {
+#pragma unroll
+                for (uint32_t b = 0; b < 4; ++b) {
+                    const uint32_t j = j0 + b;
+                    if (j >= jlo && j <= lm) {
+                        q = R.next(q, wbyte(x, b));
+                        c += q >= A;
+                    }
                 }
             }
         }
         cnt = c + chunk_count_after(ch, v, ps, T);
     }
-    if (tid == SMALL_THREADS - 1) s_misc[2] = amap(fl, v);   // the state after the text
+    if (tid == SMALL_THREADS - 1) s_misc[2] = fl == T.ident ? v : apply_map(fl, v, T.maps, nr);   // after the text
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) cnt += __shfl_down_sync(0xffffffffu, cnt, o);
     if (lane == 0) s_red[warp] = cnt;
     __syncthreads();
-    if (tid == 0) {
-        unsigned long long total = 0;
-#pragma unroll 1
-        for (int g = 0; g < G; ++g) total += s_red[g];
-        const uint32_t fin = s_misc[2];
-        sfa_result r;
-        r.final_state = (uint32_t)T.orig_of[fin < nr ? fin : 0];
-        r.accept_final = fin >= A ? 1 : 0;
-        r.status = s_misc[1] ? SFA_STATUS_TIMEOUT : SFA_STATUS_OK;
-        r.reserved = 0;
-        r.count = (carry ? out->count : 0ull) + total;
-        *out = r;
+    if (warp == 0) {
+        unsigned long long total = s_red[lane];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) total += __shfl_down_sync(0xffffffffu, total, o);
+        if (lane == 0) {
+            const uint32_t fin = s_misc[2];
+            sfa_result r;
+            r.final_state = (uint32_t)s_orig[fin < nr ? fin : 0];
+            r.accept_final = fin >= A ? 1 : 0;
+            r.status = s_misc[1] ? SFA_STATUS_TIMEOUT : SFA_STATUS_OK;
+            r.reserved = 0;
+            r.count = (carry ? out->count : 0ull) + total;
+            *out = r;
+        }
     }
 }
 
