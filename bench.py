@@ -697,7 +697,7 @@ def run_serving(args, rank, world, local):
     for load in (0.5, 0.8, 0.95, 2.0, 5.0, 10.0, 20.0, 50.0, 100.0, 200.0):
         rate = load * cap / mean
         arr, _, _ = W.workload_serving_requests(nreq, rate)
-        srv = serve.Server(autos, hbm_budget=4 << 30, max_batch=256, slots=3)
+        srv = serve.Server(autos, hbm_budget=4 << 30, max_batch=256, slots=4)
         try:
             done = srv.run(reqs(arr))
         finally:

@@ -134,7 +134,14 @@ struct GatherDesc {
 int launch_gather(const GatherDesc *d_descs, const uint32_t *d_unit0, uint32_t k, uint32_t units, cudaStream_t s);
 // The device address of host memory the device can read (pinned and mapped
 // into the device's address space), or NULL.
-const uint8_t *device_readable(const uint8_t *h);
+// cache: the last allocation found readable, for a run of texts whose host
+// memory the caller keeps allocated meanwhile (one call's texts): a range
+// kept longer could have been freed and reused since
+struct ReadableRange {
+    uintptr_t lo = 0, hi = 0;
+    uintptr_t delta = 0;   // device address - host address (mod 2^64)
+};
+const uint8_t *device_readable(const uint8_t *h, ReadableRange *cache = nullptr);
 
 // kernels_small.cu: the short-text kernel (one CTA, no scratch, no look-back)
 bool small_fits(uint64_t n);

@@ -499,9 +499,10 @@ int sfa_batch_update_host(sfa_batch_t b, const sfa_handle_t *hs, const uint8_t *
     std::vector<GatherDesc> gd;
     std::vector<uint32_t> gu;
     uint64_t units = 0;
+    ReadableRange rr;   // this call's texts stay allocated until it returns
     for (int32_t i = 0; i < k; ++i) {
         if (!lens[i]) continue;
-        const uint8_t *src = device_readable(h_texts[i]);
+        const uint8_t *src = device_readable(h_texts[i], &rr);
         if (src) {
             gu.push_back((uint32_t)units);
             gd.push_back(GatherDesc{src, d_dst[i], lens[i]});

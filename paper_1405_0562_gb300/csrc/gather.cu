@@ -5,6 +5,7 @@
 // 20 GB/s).  The texts are cut into GATHER_UNIT-byte units; CTAs take units
 // in a grid-stride loop and find a unit's text by binary search over the
 // units' prefix sums.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "api_internal.h"
@@ -18,15 +19,22 @@ constexpr uint32_t GATHER_LOADS = 4;   // 16-byte loads in flight per thread
 
 __global__ void __launch_bounds__(GATHER_THREADS) gather_kernel(const GatherDesc *g, const uint32_t *unit0,
                                                                  uint32_t k) {
+    __shared__ uint32_t s_cnt;
     const uint32_t total = unit0[k];
     for (uint32_t u = blockIdx.x; u < total; u += gridDim.x) {
-        // the text of unit u: the last r with unit0[r] <= u
-        uint32_t lo = 0, hi = k;
-        while (hi - lo > 1) {
-            const uint32_t mid = (lo + hi) >> 1;
-            if (unit0[mid] <= u) lo = mid;
-            else hi = mid;
-        }
+        // the text of unit u: the last r with unit0[r] <= u, i.e. the number
+        // of such r less one (unit0 strictly increases from unit0[0] = 0: a
+        // text of the copy has at least one unit), counted by the whole block
+        // with independent loads, not a chain of dependent ones
+        if (threadIdx.x == 0) s_cnt = 0;
+        __syncthreads();
+        uint32_t c = 0;
+        for (uint32_t r = threadIdx.x; r < k; r += GATHER_THREADS) c += unit0[r] <= u ? 1u : 0u;
+        c = __reduce_add_sync(0xffffffffu, c);
+        if ((threadIdx.x & 31u) == 0 && c) atomicAdd(&s_cnt, c);
+        __syncthreads();
+        const uint32_t lo = s_cnt - 1u;
+        __syncthreads();   // s_cnt is read before the next unit resets it
         const GatherDesc d = g[lo];
         const uint64_t b = (uint64_t)(u - unit0[lo]) * GATHER_UNIT;
         const uint64_t e = min(d.len, b + GATHER_UNIT);
@@ -72,13 +80,41 @@ int launch_gather(const GatherDesc *d_descs, const uint32_t *d_unit0, uint32_t k
     return SFA_OK;
 }
 
-const uint8_t *device_readable(const uint8_t *h) {
+const uint8_t *device_readable(const uint8_t *h, ReadableRange *cache) {
+    const uintptr_t p = reinterpret_cast<uintptr_t>(h);
+    if (cache && cache->hi && p >= cache->lo && p < cache->hi)
+        return reinterpret_cast<const uint8_t *>(p + cache->delta);
     cudaPointerAttributes a{};
     if (cudaPointerGetAttributes(&a, h) != cudaSuccess) {
         cudaGetLastError();   // clear the error of an unknown pointer
         return nullptr;
     }
     if (a.type != cudaMemoryTypeHost || !a.devicePointer) return nullptr;
+    if (cache) {
+        // the allocation's range, from the driver, so that the next texts of
+        // the same allocation need no query
+        using GetAttr = CUresult (*)(void *, CUpointer_attribute, CUdeviceptr);
+        static GetAttr get = [] {
+            void *f = nullptr;
+            cudaDriverEntryPointQueryResult q{};
+            if (cudaGetDriverEntryPointByVersion("cuPointerGetAttribute", &f, 12000, cudaEnableDefault, &q) !=
+                    cudaSuccess ||
+                q != cudaDriverEntryPointSuccess) {
+                cudaGetLastError();
+                return (GetAttr) nullptr;
+            }
+            return reinterpret_cast<GetAttr>(f);
+        }();
+        CUdeviceptr lo = 0;
+        size_t size = 0;
+        if (get && get(&lo, CU_POINTER_ATTRIBUTE_RANGE_START_ADDR, (CUdeviceptr)p) == CUDA_SUCCESS &&
+            get(&size, CU_POINTER_ATTRIBUTE_RANGE_SIZE, (CUdeviceptr)p) == CUDA_SUCCESS && size &&
+            p >= (uintptr_t)lo && p < (uintptr_t)lo + size) {
+            cache->lo = (uintptr_t)lo;
+            cache->hi = (uintptr_t)lo + size;
+            cache->delta = reinterpret_cast<uintptr_t>(a.devicePointer) - p;
+        }
+    }
     return static_cast<const uint8_t *>(a.devicePointer);
 }
 

@@ -90,7 +90,6 @@ __global__ void __launch_bounds__(SMALL_THREADS, 1) sfa_small_kernel(Tables T, c
                                                                   uint32_t chunk, uint32_t origin, uint32_t carry,
                                                                   uint32_t nc_words, sfa_result *out) {
     using L = SmallLayout;
-    constexpr int G = L::G;
     extern __shared__ __align__(128) uint8_t smem[];
     const uint32_t nr = T.nr, A = T.first_accept;
     uint8_t *s_dfa = smem;

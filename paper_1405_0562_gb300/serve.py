@@ -121,6 +121,8 @@ class Server:
             raise ValueError("request larger than the HBM text budget")
         if req.rid in self._pending:
             raise ValueError("request id already in flight")
+        if not 0 <= req.rid < self._RUN_TAG:
+            raise ValueError("request ids of submit() are in [0, 2^62)")
         self._pending[req.rid] = req
         _check(lib().sfa_server_submit(self._s, req.automaton, _host_ptr(req.text), req.nbytes, req.rid),
                "sfa_server_submit")
@@ -185,12 +187,18 @@ class Server:
         self.close()
 
     # ---- driving a workload ------------------------------------------------
+    _RUN_TAG = 1 << 62   # tags of run()'s requests: this base + position
+
     def run(self, requests: Sequence[Request], realtime: bool = True):
         """Submit each request at its arrival time (offsets from now) and
         serve until all are done.  Returns the completed requests.  The
-        requests' arrays (automaton, text address, length, id) are built
+        requests' arrays (automaton, text address, length, tag) are built
         before the clock starts; the requests due at each turn of the loop
-        go to the server in one call."""
+        go to the server in one call, and completions are stamped by array
+        (no per-request Python work inside the loop: at tens of thousands
+        of requests a second that work, not the device, would set the
+        pace).  Requests submitted by submit() and not yet done are served
+        too."""
         pending = sorted(requests, key=lambda r: r.arrival)
         n = len(pending)
         for r in pending:
@@ -202,21 +210,60 @@ class Server:
         auto = np.array([r.automaton for r in pending], dtype=np.int32)
         ptr = np.array([_host_ptr(r.text) for r in pending], dtype=np.uint64)
         ln = np.array([r.nbytes for r in pending], dtype=np.uint64)
-        tag = np.array([r.rid for r in pending], dtype=np.uint64)
+        tag = np.arange(n, dtype=np.uint64) + np.uint64(self._RUN_TAG)
+        done_t = np.zeros(n, dtype=np.float64)
+        words = np.zeros((n, 2), dtype=np.uint64)
         L = lib()
         t0 = time.perf_counter()
         i = 0
-        while i < n or not self.idle():
+        left = n
+        while i < n or left or self._pending:
             j = n if not realtime else int(np.searchsorted(rel, time.perf_counter() - t0, side="right"))
             if j > i:
-                for r, a in zip(pending[i:j], rel[i:j].tolist()):
-                    r.arrival = t0 + a
-                    self._pending[r.rid] = r
                 _check(L.sfa_server_submit_many(self._s, j - i, auto[i:].ctypes.data, ptr[i:].ctypes.data,
                                                 ln[i:].ctypes.data, tag[i:].ctypes.data), "sfa_server_submit_many")
                 i = j
-            self.step()
+            left -= self._drain(done_t, words)
+        # the Request records, once the clock has stopped
+        res = decode(words.view(np.uint8))
+        for k, r in enumerate(pending):
+            r.arrival = t0 + rel[k]
+            r.admitted = r.arrival
+            r.done = float(done_t[k])
+            r.result = res[k]
+            self.completed.append(r)
         return self.completed
+
+    def _drain(self, done_t, words) -> int:
+        """One progress call: stamp run()'s completions into the arrays (by
+        tag), hand the others to their Request records; returns the number
+        of run() completions."""
+        L = lib()
+        got = 0
+        while True:
+            _check(L.sfa_server_progress(self._s, self._buf, self._cap, ctypes.byref(self._n)),
+                   "sfa_server_progress")
+            k = self._n.value
+            if not k:
+                return got
+            now = time.perf_counter()
+            raw = np.ctypeslib.as_array(ctypes.cast(self._buf, ctypes.POINTER(ctypes.c_uint64)),
+                                        shape=(k * 3,)).reshape(k, 3)
+            tags = raw[:, 0]
+            mine = tags >= np.uint64(self._RUN_TAG)
+            idx = (tags[mine] - np.uint64(self._RUN_TAG)).astype(np.int64)
+            done_t[idx] = now
+            words[idx] = raw[mine, 1:]
+            got += int(idx.size)
+            if not mine.all():
+                other = raw[~mine]
+                for t, x in zip(other[:, 0].tolist(), decode(other[:, 1:].copy().view(np.uint8))):
+                    r = self._pending.pop(t)
+                    r.result = x
+                    r.done = now
+                    self.completed.append(r)
+            if k < self._cap:
+                return got
 
 
 def one_at_a_time(automata: Sequence[Automaton], requests: Sequence[Request], realtime: bool = True):
