@@ -143,7 +143,8 @@ struct ReadableRange {
 };
 const uint8_t *device_readable(const uint8_t *h, ReadableRange *cache = nullptr);
 
-// kernels_small.cu: the short-text kernel (one CTA, no scratch, no look-back)
+// kernels_small.cu: the short-text kernel (one CTA or a cluster of up to 16,
+// no scratch, no look-back); texts of up to 1 MiB
 bool small_fits(uint64_t n);
 // n_nc: the handle's stored non-constant rows (staged in shared memory when
 // they fit)

@@ -13,8 +13,21 @@
 // non-constant rows are staged in shared memory when they fit (pass 1 then
 // never waits on L2), and the scans and the final sum use warp ballots and
 // shuffles instead of loops over shared memory.
+//
+// Past one CTA's 64 KiB (and for latency already past 16 KiB) the same
+// kernel runs as a thread-block cluster of up to 16 CTAs, each matching a
+// contiguous run of chunks: every CTA composes its groups into its aggregate
+// (a constant, f_I, or a |Q|-vector), and after a cluster barrier reads the
+// aggregates of the CTAs before it from their shared memory (Lemma 1 across
+// CTAs, no global scratch and no wait on a flag); the counts are added into
+// CTA 0's shared memory, which writes the result after a second barrier.
+#include <cooperative_groups.h>
+
 #include <algorithm>
 #include <atomic>
+#include <mutex>
+#include <utility>
+#include <vector>
 
 #include "api_internal.h"
 #include "sfa_device.cuh"
@@ -24,6 +37,7 @@ namespace sfa_dev {
 constexpr int SMALL_THREADS = 1024;
 constexpr int SMALL_CHUNK = 64;               // bytes per chunk at most (chunk 0: up to 15 more)
 constexpr int SMALL_WORDS = (SMALL_CHUNK + 16) / 4;
+constexpr int SMALL_CLUSTER_MAX = 16;         // CTAs of a cluster at most (a non-portable size)
 
 struct SmallLayout {
     static constexpr int G = SMALL_THREADS / 32;
@@ -34,9 +48,12 @@ struct SmallLayout {
     static SFA_HD size_t gpre_off(uint32_t nr) { return gval_off(nr) + G * 4; }
     static SFA_HD size_t red_off(uint32_t nr) { return gpre_off(nr) + G * 4; }
     static SFA_HD size_t misc_off(uint32_t nr) { return red_off(nr) + G * 8; }
-    static SFA_HD size_t txt_off(uint32_t nr) { return misc_off(nr) + 16; }
+    // cluster exchange: aggregate kind and value, final state, count (u64)
+    static SFA_HD size_t clu_off(uint32_t nr) { return misc_off(nr) + 16; }
+    static SFA_HD size_t txt_off(uint32_t nr) { return clu_off(nr) + 32; }
     static SFA_HD size_t gvec_off(uint32_t nr) { return txt_off(nr) + (size_t)SMALL_WORDS * SMALL_THREADS * 4; }
-    static SFA_HD size_t orig_off(uint32_t nr) { return a16(gvec_off(nr) + (size_t)G * nr); }
+    static SFA_HD size_t aggv_off(uint32_t nr) { return gvec_off(nr) + (size_t)G * nr; }   // the CTA's vector
+    static SFA_HD size_t orig_off(uint32_t nr) { return a16(aggv_off(nr) + nr); }
     static SFA_HD size_t nc_off(uint32_t nr) { return a16(orig_off(nr) + (size_t)nr * 4); }
     static SFA_HD size_t bytes(uint32_t nr) { return nc_off(nr); }
     // with the non-constant rows (nc_words 32-bit entries) staged
@@ -46,6 +63,8 @@ static_assert(SmallLayout::G == 32, "the group scans are one warp wide");
 
 constexpr uint32_t GV_IDENT = 0xfffffffeu;    // a group of f_I chunks (past the text)
 constexpr uint32_t GV_VEC = 0xffffffffu;      // a group summarised by a |Q|-vector
+// kinds of a CTA's aggregate in a cluster
+constexpr uint32_t AGG_IDENT = 0, AGG_CONST = 1, AGG_VEC = 2;
 
 // asynchronous global -> shared copies (no register holds the data)
 __device__ __forceinline__ void cp_async4(void *dst, const void *src) {
@@ -102,6 +121,13 @@ __global__ void __launch_bounds__(SMALL_THREADS, 1) sfa_small_kernel(Tables T, c
     uint32_t *s_txt = reinterpret_cast<uint32_t *>(smem + L::txt_off(nr));
     uint8_t *s_gvec = smem + L::gvec_off(nr);
     int32_t *s_orig = reinterpret_cast<int32_t *>(smem + L::orig_off(nr));
+    uint32_t *s_clu = reinterpret_cast<uint32_t *>(smem + L::clu_off(nr));
+    unsigned long long *s_total = reinterpret_cast<unsigned long long *>(smem + L::clu_off(nr) + 16);
+    uint8_t *s_aggv = smem + L::aggv_off(nr);
+    namespace cg = cooperative_groups;
+    const cg::cluster_group cluster = cg::this_cluster();
+    const uint32_t crank = cluster.block_rank(), csize = cluster.num_blocks();
+    const uint32_t gt = crank * SMALL_THREADS + (uint32_t)threadIdx.x;   // this thread's chunk
     uint32_t *s_nc = reinterpret_cast<uint32_t *>(smem + L::nc_off(nr));
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t lanemask_lt = (1u << lane) - 1u;
@@ -114,10 +140,10 @@ __global__ void __launch_bounds__(SMALL_THREADS, 1) sfa_small_kernel(Tables T, c
     // t > 0 is [origin + t * chunk, origin + (t + 1) * chunk) (Theorem 3: any
     // division); window bytes [jlo, jhi) are the chunk's.
     const uint32_t head = origin ? 16u - origin : 0u, o16 = head + origin;
-    const uint64_t vs = tid == 0 ? 0 : (uint64_t)o16 + (uint64_t)tid * chunk;
-    const uint64_t ve_c = (uint64_t)o16 + (uint64_t)(tid + 1) * chunk, ve_t = (uint64_t)head + n;
+    const uint64_t vs = gt == 0 ? 0 : (uint64_t)o16 + (uint64_t)gt * chunk;
+    const uint64_t ve_c = (uint64_t)o16 + (uint64_t)(gt + 1) * chunk, ve_t = (uint64_t)head + n;
     const uint64_t ve = ve_c < ve_t ? ve_c : ve_t;
-    const uint32_t jlo = tid == 0 ? head : 0u;
+    const uint32_t jlo = gt == 0 ? head : 0u;
     const uint32_t jhi = ve > vs ? (uint32_t)(ve - vs) : 0u;
 
     // the chunk's full 16-byte units into registers
@@ -255,8 +281,72 @@ __global__ void __launch_bounds__(SMALL_THREADS, 1) sfa_small_kernel(Tables T, c
         }
         s_misc[0] = s_in;
         s_misc[1] = bad;
+        if (crank == 0) *s_total = 0;
     }
     __syncthreads();
+    if (csize > 1) {
+        // this CTA's aggregate (warp 0): its groups composed in order
+        if (warp == 0) {
+            const uint32_t gv = s_gval[lane];
+            const uint32_t cgm = __ballot_sync(0xffffffffu, gv < GV_IDENT);
+            const uint32_t vgm = __ballot_sync(0xffffffffu, gv == GV_VEC);
+            if (cgm) {
+                const int j = 31 - __clz(cgm);
+                uint32_t v = __shfl_sync(0xffffffffu, gv, j);
+                uint32_t m = vgm & ~((2u << j) - 1u);
+#pragma unroll 1
+                while (m) {
+                    const int g = __ffs(m) - 1;
+                    m &= m - 1u;
+                    v = s_gvec[(size_t)g * nr + v];
+                }
+                if (lane == 0) {
+                    s_clu[0] = AGG_CONST;
+                    s_clu[1] = v;
+                }
+            } else if (!vgm) {
+                if (lane == 0) s_clu[0] = AGG_IDENT;
+            } else {
+#pragma unroll 1
+                for (uint32_t q = lane; q < nr; q += 32) {
+                    uint32_t v = q, m = vgm;
+#pragma unroll 1
+                    while (m) {
+                        const int g = __ffs(m) - 1;
+                        m &= m - 1u;
+                        v = s_gvec[(size_t)g * nr + v];
+                    }
+                    s_aggv[q] = (uint8_t)v;
+                }
+                if (lane == 0) s_clu[0] = AGG_VEC;
+            }
+        }
+        cluster.sync();   // every aggregate written
+        // the state entering this CTA (warp 0; lane j reads CTA j's kind):
+        // the last constant aggregate before it, then the vectors after that
+        if (warp == 0) {
+            uint32_t kind = AGG_IDENT, val = 0;
+            if ((uint32_t)lane < crank) {
+                const uint32_t *rc = cluster.map_shared_rank(s_clu, (int)lane);
+                kind = rc[0];
+                val = rc[1];
+            }
+            const uint32_t ccm = __ballot_sync(0xffffffffu, kind == AGG_CONST);
+            const uint32_t cvm = __ballot_sync(0xffffffffu, kind == AGG_VEC);
+            const int j = ccm ? 31 - __clz(ccm) : -1;
+            const uint32_t vj = __shfl_sync(0xffffffffu, val, j < 0 ? 0 : j);
+            uint32_t st = j < 0 ? s_misc[0] : vj;
+            uint32_t m = cvm & (j < 0 ? 0xffffffffu : ~((2u << j) - 1u));
+#pragma unroll 1
+            while (m) {
+                const int r = __ffs(m) - 1;
+                m &= m - 1u;
+                st = cluster.map_shared_rank(s_aggv, r)[st];
+            }
+            if (lane == 0) s_misc[0] = st;
+        }
+        __syncthreads();
+    }
     // exclusive prefix of every group (warp 0, lane g for group g): the
     // nearest constant group below it, then the vector groups in between
     if (warp == 0) {
@@ -327,15 +417,26 @@ __global__ void __launch_bounds__(SMALL_THREADS, 1) sfa_small_kernel(Tables T, c
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) total += __shfl_down_sync(0xffffffffu, total, o);
         if (lane == 0) {
-            const uint32_t fin = s_misc[2];
-            sfa_result r;
-            r.final_state = (uint32_t)s_orig[fin < nr ? fin : 0];
-            r.accept_final = fin >= A ? 1 : 0;
-            r.status = s_misc[1] ? SFA_STATUS_TIMEOUT : SFA_STATUS_OK;
-            r.reserved = 0;
-            r.count = (carry ? out->count : 0ull) + total;
-            *out = r;
+            if (csize > 1) {
+                // into CTA 0: the count, and from the last CTA the state after the text
+                atomicAdd(cluster.map_shared_rank(s_total, 0), total);
+                if (crank == csize - 1) *cluster.map_shared_rank(s_clu + 2, 0) = s_misc[2];
+            } else {
+                *s_total = total;
+                s_clu[2] = s_misc[2];
+            }
         }
+    }
+    if (csize > 1) cluster.sync();   // every count added; no CTA leaves while others read its memory
+    if (crank == 0 && tid == 0) {
+        const uint32_t fin = s_clu[2];
+        sfa_result r;
+        r.final_state = (uint32_t)s_orig[fin < nr ? fin : 0];
+        r.accept_final = fin >= A ? 1 : 0;
+        r.status = s_misc[1] ? SFA_STATUS_TIMEOUT : SFA_STATUS_OK;
+        r.reserved = 0;
+        r.count = (carry ? out->count : 0ull) + *s_total;
+        *out = r;
     }
 }
 
@@ -343,36 +444,102 @@ __global__ void __launch_bounds__(SMALL_THREADS, 1) sfa_small_kernel(Tables T, c
 
 namespace sfa_impl {
 
-bool small_fits(uint64_t n) { return n <= (uint64_t)sfa_dev::SMALL_THREADS * sfa_dev::SMALL_CHUNK; }
+namespace {
+
+constexpr uint64_t CLUSTER_FROM = 16 << 10;   // longer texts take a cluster of CTAs,
+constexpr uint64_t CTA_BYTES = 16 << 10;      // about this many bytes each
+
+// whether clusters of c CTAs of this shape can be resident on the device,
+// asked once per (device, c, shared-memory size)
+bool cluster_fits(int dev, int c, size_t smem) {
+    static std::mutex mu;
+    static std::vector<std::pair<std::pair<int, int>, std::pair<size_t, bool>>> known;
+    std::lock_guard<std::mutex> lock(mu);
+    for (auto &e : known)
+        if (e.first.first == dev && e.first.second == c && e.second.first == smem) return e.second.second;
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)c);
+    cfg.blockDim = dim3(sfa_dev::SMALL_THREADS);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = (unsigned)c;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int nclusters = 0;
+    const bool ok = cudaOccupancyMaxActiveClusters(&nclusters, reinterpret_cast<const void *>(&sfa_dev::sfa_small_kernel),
+                                                   &cfg) == cudaSuccess &&
+                    nclusters > 0;
+    if (!ok) cudaGetLastError();
+    known.push_back({{dev, c}, {smem, ok}});
+    return ok;
+}
+
+}  // namespace
+
+bool small_fits(uint64_t n) {
+    return n <= (uint64_t)sfa_dev::SMALL_CLUSTER_MAX * sfa_dev::SMALL_THREADS * sfa_dev::SMALL_CHUNK;
+}
 
 size_t small_smem(uint32_t nr) { return sfa_dev::SmallLayout::bytes(nr); }
 
 int launch_small(const sfa_dev::Tables &T, uint64_t n_nc, const uint8_t *text, uint64_t n, bool carry,
                  sfa_result *out, cudaStream_t s) {
     if (!small_fits(n) || T.nr > 255) return SFA_ERR_UNSUPPORTED;
-    // chunk bodies from the first 16-byte boundary, in 16-byte multiples
-    const uint32_t origin = n ? sfa_dev::text_origin(text) : 0u;
-    const uint64_t body = n > origin ? n - origin : 0;
-    uint32_t chunk = (uint32_t)((body + sfa_dev::SMALL_THREADS - 1) / sfa_dev::SMALL_THREADS);
-    chunk = std::max<uint32_t>(16, (chunk + 15) & ~15u);
-    if (chunk > (uint32_t)sfa_dev::SMALL_CHUNK) return SFA_ERR_UNSUPPORTED;
-    // the kernel's shared-memory limit, raised once per device
-    static std::atomic<uint8_t> attr_done[64];
     int dev = 0;
     CK(cudaGetDevice(&dev));
-    const size_t optin = device_props(dev).smem_optin;
     if (dev < 0 || dev >= 64) return SFA_ERR_UNSUPPORTED;
+    const size_t optin = device_props(dev).smem_optin;
+    // the kernel's shared-memory limit and cluster size, raised once per device
+    static std::atomic<uint8_t> attr_done[64];
     if (!attr_done[dev].load(std::memory_order_acquire)) {
-        CK(cudaFuncSetAttribute(reinterpret_cast<const void *>(&sfa_dev::sfa_small_kernel),
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)optin));
+        const void *k = reinterpret_cast<const void *>(&sfa_dev::sfa_small_kernel);
+        CK(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)optin));
+        CK(cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
         attr_done[dev].store(1, std::memory_order_release);
     }
     // the non-constant rows go to shared memory when they fit
     const uint64_t nc_words = n_nc * T.ncls;
     const bool stage = nc_words && sfa_dev::SmallLayout::bytes(T.nr, nc_words) <= optin;
     const size_t smem = stage ? sfa_dev::SmallLayout::bytes(T.nr, nc_words) : small_smem(T.nr);
-    sfa_dev::sfa_small_kernel<<<1, sfa_dev::SMALL_THREADS, smem, s>>>(T, text, n, chunk, origin, carry ? 1u : 0u,
-                                                                     stage ? (uint32_t)nc_words : 0u, out);
+    // CTAs: one up to CLUSTER_FROM bytes, then about CTA_BYTES each (fewer if
+    // a cluster that large cannot be resident, while every chunk stays within
+    // SMALL_CHUNK bytes)
+    const uint32_t origin = n ? sfa_dev::text_origin(text) : 0u;
+    const uint64_t body = n > origin ? n - origin : 0;
+    int c = n <= CLUSTER_FROM ? 1
+                              : (int)std::min<uint64_t>(sfa_dev::SMALL_CLUSTER_MAX, (n + CTA_BYTES - 1) / CTA_BYTES);
+    const uint64_t cap_cta = (uint64_t)sfa_dev::SMALL_THREADS * sfa_dev::SMALL_CHUNK;
+    while (c > 1 && !cluster_fits(dev, c, smem)) {
+        if ((uint64_t)(c - 1) * cap_cta < body + 16) return SFA_ERR_UNSUPPORTED;   // the persistent kernel takes it
+        --c;
+    }
+    // chunk bodies from the first 16-byte boundary, in 16-byte multiples
+    const uint64_t threads = (uint64_t)c * sfa_dev::SMALL_THREADS;
+    uint32_t chunk = (uint32_t)((body + threads - 1) / threads);
+    chunk = std::max<uint32_t>(16, (chunk + 15) & ~15u);
+    if (chunk > (uint32_t)sfa_dev::SMALL_CHUNK) return SFA_ERR_UNSUPPORTED;
+    const uint32_t nc_arg = stage ? (uint32_t)nc_words : 0u, carry_arg = carry ? 1u : 0u;
+    if (c == 1) {
+        sfa_dev::sfa_small_kernel<<<1, sfa_dev::SMALL_THREADS, smem, s>>>(T, text, n, chunk, origin, carry_arg,
+                                                                         nc_arg, out);
+    } else {
+        cudaLaunchConfig_t cfg{};
+        cfg.gridDim = dim3((unsigned)c);
+        cfg.blockDim = dim3(sfa_dev::SMALL_THREADS);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = s;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = (unsigned)c;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        CK(cudaLaunchKernelEx(&cfg, &sfa_dev::sfa_small_kernel, T, text, n, chunk, origin, carry_arg, nc_arg, out));
+    }
     CK(cudaGetLastError());
     g_launches.fetch_add(1, std::memory_order_relaxed);
     return SFA_OK;

@@ -486,13 +486,16 @@ int match_impl(sfa_handle *h, const uint8_t *d_text, uint64_t n, sfa_result *d_o
     // the slice mapping is composed from CTA-tile aggregates of byte ids
     if (d_map && o && o->tiling == SFA_TILING_WARP) return SFA_ERR_INVALID;
     if (d_map && h->host.wide) return SFA_ERR_UNSUPPORTED;
-    // a short text with the automatic shape: one CTA, no scratch (its
-    // latency is a kernel launch and the text's dependent lookups)
+    // a text of up to 1 MiB with the automatic shape: one CTA or one cluster
+    // of CTAs, no scratch (its latency is a kernel launch and the text's
+    // dependent lookups); UNSUPPORTED when no such cluster can be resident
     const bool shape_given = o && (o->chunk_bytes || o->block_threads || o->chains || o->max_ctas ||
                                    o->forced_chunks || o->debug_flags || o->tiling);
     if (!d_map && !shape_given && h->host.mode == SFA_MODE_SFA && !h->host.wide && h->host.nr <= 255 &&
-        small_fits(n))
-        return launch_small(h->dev, h->host.n_nc, d_text, n, carry, d_out, s);
+        small_fits(n)) {
+        const int rc = launch_small(h->dev, h->host.n_nc, d_text, n, carry, d_out, s);
+        if (rc != SFA_ERR_UNSUPPORTED) return rc;   // else: the persistent kernel below
+    }
     Shape sh;
     int rc = choose_shape(h, n, o, sh);
     if (rc) return rc;

@@ -115,9 +115,10 @@ SMALL_LENS = [0, 1, 2, 15, 16, 17, 31, 63, 64, 65, 1000, 1023, 1024, 1025, 16383
 
 @pytest.mark.parametrize("name", sorted(AUTOMATA))
 def test_short_texts_one_cta(name):
-    """Texts up to 64 KiB with the automatic shape take the one-CTA kernel
-    (no scratch, no look-back): every length around its chunk sizes (16 to
-    64 bytes per thread) and its 64 KiB limit, every start offset modulo 16,
+    """Texts up to 16 KiB with the automatic shape take the one-CTA kernel
+    (no scratch, no look-back), longer ones up to 1 MiB a cluster of such
+    CTAs: every length around the chunk sizes (16 to 64 bytes per thread),
+    the one-CTA limit and the first cluster sizes, start offsets modulo 16,
     and Lemma 1 streaming with short pieces.  Simulation-mode handles and
     explicit shapes keep the persistent kernel."""
     sfa = sfa_mod()
@@ -134,6 +135,48 @@ def test_short_texts_one_cta(name):
             assert sfa.decode(out)[0] == expect(d, base[off:off + n]), (name, n, off)
     # Lemma 1 pieces of a few hundred bytes, then one past the limit
     cuts = [0, 5, 300, 301, 4000, 20000, 65536 + 3, base.size]
+    out = a.match(dev[:cuts[1]])
+    for i in range(1, len(cuts) - 1):
+        a.match_continue(dev[cuts[i]:cuts[i + 1]], out)
+    torch.cuda.synchronize()
+    assert sfa.decode(out)[0] == expect(d, base)
+
+
+def _perm7():
+    """Sum of the bytes mod 7: every symbol permutes the states, so no chunk
+    mapping is ever constant (every group and CTA aggregate is a vector)."""
+    q = np.arange(7, dtype=np.int64)[:, None]
+    b = np.arange(256, dtype=np.int64)[None, :]
+    acc = np.zeros(7, np.uint8)
+    acc[0] = 1
+    return W.DFA(((q + b) % 7).astype(np.int32), 0, acc, bytes(range(97, 105)), name="perm7")
+
+
+CLUSTER_LENS = [16385, 20000, 32769, 65537, 100_003, 131_072, 262_147, 524_287, (1 << 20) - 1, 1 << 20]
+
+
+@pytest.mark.parametrize("name", ["ac_set", "r5", "ra2", "T4", "rand8", "one_state", "single", "perm7"])
+def test_short_texts_cluster(name):
+    """Texts of 16 KiB to 1 MiB take the cluster form of the short-text
+    kernel (2 to 16 CTAs exchanging their aggregates through distributed
+    shared memory): lengths from just past one CTA to the 1 MiB limit and
+    just past it (the persistent kernel), unaligned starts, and Lemma 1
+    streaming across pieces of cluster size.  perm7 keeps every aggregate a
+    |Q|-vector; ac_set's are constants; r5/ra2's point and set-point
+    mappings."""
+    sfa = sfa_mod()
+    d = _perm7() if name == "perm7" else AUTOMATA[name]()
+    a = sfa.Automaton.from_dfa(d)
+    base = text_for(d, (1 << 20) + 4096, seed=len(name) + 11)
+    dev = torch.from_numpy(base).cuda()
+    for n in CLUSTER_LENS + [(1 << 20) + 1]:
+        for off in (0, 9):
+            if off + n > base.size:
+                continue
+            out = a.match(dev[off:off + n])
+            torch.cuda.synchronize()
+            assert sfa.decode(out)[0] == expect(d, base[off:off + n]), (name, n, off)
+    cuts = [0, 3, 40_000, 40_001, 300_000, 300_016, 1_000_000, base.size]
     out = a.match(dev[:cuts[1]])
     for i in range(1, len(cuts) - 1):
         a.match_continue(dev[cuts[i]:cuts[i + 1]], out)
