@@ -447,7 +447,7 @@ namespace sfa_impl {
 namespace {
 
 constexpr uint64_t CLUSTER_FROM = 16 << 10;   // longer texts take a cluster of CTAs,
-constexpr uint64_t CTA_BYTES = 16 << 10;      // about this many bytes each
+constexpr uint64_t CTA_BYTES = 8 << 10;       // about this many bytes each
 
 // whether clusters of c CTAs of this shape can be resident on the device,
 // asked once per (device, c, shared-memory size)

@@ -20,6 +20,7 @@ from __future__ import annotations
 
 import ctypes
 import dataclasses
+import gc
 import time
 from typing import Dict, List, Optional, Sequence
 
@@ -214,16 +215,25 @@ class Server:
         done_t = np.zeros(n, dtype=np.float64)
         words = np.zeros((n, 2), dtype=np.uint64)
         L = lib()
-        t0 = time.perf_counter()
-        i = 0
-        left = n
-        while i < n or left or self._pending:
-            j = n if not realtime else int(np.searchsorted(rel, time.perf_counter() - t0, side="right"))
-            if j > i:
-                _check(L.sfa_server_submit_many(self._s, j - i, auto[i:].ctypes.data, ptr[i:].ctypes.data,
-                                                ln[i:].ctypes.data, tag[i:].ctypes.data), "sfa_server_submit_many")
-                i = j
-            left -= self._drain(done_t, words)
+        # no cyclic garbage collection inside the loop: with many live
+        # objects in the process one collection stalls admission for
+        # milliseconds
+        gc_on = gc.isenabled()
+        gc.disable()
+        try:
+            t0 = time.perf_counter()
+            i = 0
+            left = n
+            while i < n or left or self._pending:
+                j = n if not realtime else int(np.searchsorted(rel, time.perf_counter() - t0, side="right"))
+                if j > i:
+                    _check(L.sfa_server_submit_many(self._s, j - i, auto[i:].ctypes.data, ptr[i:].ctypes.data,
+                                                    ln[i:].ctypes.data, tag[i:].ctypes.data), "sfa_server_submit_many")
+                    i = j
+                left -= self._drain(done_t, words)
+        finally:
+            if gc_on:
+                gc.enable()
         # the Request records, once the clock has stopped
         res = decode(words.view(np.uint8))
         for k, r in enumerate(pending):
