@@ -38,6 +38,7 @@ constexpr int SMALL_THREADS = 1024;
 constexpr int SMALL_CHUNK = 64;               // bytes per chunk at most (chunk 0: up to 15 more)
 constexpr int SMALL_WORDS = (SMALL_CHUNK + 16) / 4;
 constexpr int SMALL_CLUSTER_MAX = 16;         // CTAs of a cluster at most (a non-portable size)
+constexpr uint32_t SMALL_WAIT_US = 2000000;   // bound of the one wait (for the bulk copy)
 
 struct SmallLayout {
     static constexpr int G = SMALL_THREADS / 32;
@@ -48,7 +49,8 @@ struct SmallLayout {
     static SFA_HD size_t gpre_off(uint32_t nr) { return gval_off(nr) + G * 4; }
     static SFA_HD size_t red_off(uint32_t nr) { return gpre_off(nr) + G * 4; }
     static SFA_HD size_t misc_off(uint32_t nr) { return red_off(nr) + G * 8; }
-    // cluster exchange: aggregate kind and value, final state, count (u64)
+    // cluster exchange: aggregate kind and value, final state, count (u64);
+    // then the mbarrier of the bulk copy of the non-constant rows
     static SFA_HD size_t clu_off(uint32_t nr) { return misc_off(nr) + 16; }
     static SFA_HD size_t txt_off(uint32_t nr) { return clu_off(nr) + 32; }
     static SFA_HD size_t gvec_off(uint32_t nr) { return txt_off(nr) + (size_t)SMALL_WORDS * SMALL_THREADS * 4; }
@@ -146,6 +148,20 @@ __global__ void __launch_bounds__(SMALL_THREADS, 1) sfa_small_kernel(Tables T, c
     const uint32_t jlo = gt == 0 ? head : 0u;
     const uint32_t jhi = ve > vs ? (uint32_t)(ve - vs) : 0u;
 
+    // the non-constant rows by one bulk copy (the largest table; the copy
+    // engine moves it faster than per-thread copies would)
+    uint32_t *s_err = s_misc + 3;   // a bounded wait gave up
+    const uint32_t bar = smem_addr(smem + L::clu_off(nr) + 24);
+    const uint32_t nc16 = (nc_words + 3) / 4;
+    if (tid == 0) {
+        *s_err = 0;
+        if (nc16) {
+            mbar_init(bar, 1);
+            mbar_init_fence();
+            mbar_arrive_expect_tx(bar, nc16 * 16);
+            bulk_copy(smem_addr(s_nc), reinterpret_cast<const uint8_t *>(T.nc), nc16 * 16, bar);
+        }
+    }
     // the chunk's full 16-byte units into registers
     uint4 tx[SMALL_WORDS / 4];
 #pragma unroll
@@ -154,18 +170,14 @@ __global__ void __launch_bounds__(SMALL_THREADS, 1) sfa_small_kernel(Tables T, c
         tx[u] = make_uint4(0, 0, 0, 0);
         if (jlo <= a && a + 16 <= jhi) tx[u] = ldg128(text + (vs + a - head));
     }
-    // the tables by asynchronous copies: DFA rows in 8-byte pieces (rows ROWB
-    // apart), the class table, the caller's state ids, the non-constant rows
-    // when staged (their region is 256-byte aligned and padded: whole 16-byte
-    // units are read)
+    // the other tables by asynchronous copies: DFA rows in 8-byte pieces (rows
+    // ROWB apart, not all 16-byte aligned), the class table, the caller's
+    // state ids
 #pragma unroll 1
     for (uint32_t i = tid; i < nr * 32; i += SMALL_THREADS)
         cp_async8(s_dfa + (i >> 5) * ROWB + (i & 31) * 8, T.dfa + (size_t)i * 8);
     if (tid < 16) cp_async16(s_cls + tid * 16, T.cls + tid * 16);
     if ((uint32_t)tid < nr) cp_async4(s_orig + tid, T.orig_of + tid);
-    const uint32_t nc16 = (nc_words + 3) / 4;
-#pragma unroll 1
-    for (uint32_t i = tid; i < nc16; i += SMALL_THREADS) cp_async16(s_nc + 4 * i, T.nc + 4 * i);
     const uint32_t *ncp = nc_words ? s_nc : T.nc;
     // the text's first or last partial 16 bytes (chunk 0 and the last chunk)
 #pragma unroll 1
@@ -194,6 +206,9 @@ __global__ void __launch_bounds__(SMALL_THREADS, 1) sfa_small_kernel(Tables T, c
     }
     cp_async_wait_all();
     __syncthreads();
+    // the non-constant rows (the staged region is 256-byte aligned and padded
+    // in global memory: whole 16-byte units are read); a bounded wait
+    if (nc16) wait_stage(bar, 0u, s_err, SMALL_WAIT_US);
 
     // pass 1: the chunk from f_I, one word (4 bytes) per iteration; a word
     // entered with a constant mapping is four DFA-row lookups
@@ -418,8 +433,10 @@ __global__ void __launch_bounds__(SMALL_THREADS, 1) sfa_small_kernel(Tables T, c
         for (int o = 16; o > 0; o >>= 1) total += __shfl_down_sync(0xffffffffu, total, o);
         if (lane == 0) {
             if (csize > 1) {
-                // into CTA 0: the count, and from the last CTA the state after the text
+                // into CTA 0: the count, a wait that gave up, and from the
+                // last CTA the state after the text
                 atomicAdd(cluster.map_shared_rank(s_total, 0), total);
+                if (*(volatile uint32_t *)s_err) atomicOr(cluster.map_shared_rank(s_err, 0), 1u);
                 if (crank == csize - 1) *cluster.map_shared_rank(s_clu + 2, 0) = s_misc[2];
             } else {
                 *s_total = total;
@@ -433,11 +450,14 @@ __global__ void __launch_bounds__(SMALL_THREADS, 1) sfa_small_kernel(Tables T, c
         sfa_result r;
         r.final_state = (uint32_t)s_orig[fin < nr ? fin : 0];
         r.accept_final = fin >= A ? 1 : 0;
-        r.status = s_misc[1] ? SFA_STATUS_TIMEOUT : SFA_STATUS_OK;
+        r.status = s_misc[1] || *(volatile uint32_t *)s_err ? SFA_STATUS_TIMEOUT : SFA_STATUS_OK;
         r.reserved = 0;
         r.count = (carry ? out->count : 0ull) + *s_total;
         *out = r;
     }
+    // a wait that gave up: the bulk copy may still be landing; a bounded wait
+    // for it before the CTA's shared memory is released
+    if (tid == 0 && nc16 && *(volatile uint32_t *)s_err) drain_stages(bar, 1u, 1, SMALL_WAIT_US);
 }
 
 }  // namespace sfa_dev
