@@ -802,6 +802,23 @@ def run_crossover(args, rank, world, local):
     import oracle
     import paper_1405_0562_gb300 as sfa
     torch.cuda.set_device(local)
+    if args.profile:
+        # for ncu: 4 matches each of the first 1 KiB (one CTA of the
+        # short-text kernel), 64 KiB (a cluster of 8) and 1 MiB (a cluster of
+        # 16), no graphs, the last of each size checked against the oracle
+        d, t = W.workload_large(1 << 20)
+        a = sfa.Automaton.from_dfa(d, sample=t)
+        out = sfa.empty_results(1)
+        for n in (1 << 10, 64 << 10, 1 << 20):
+            tt = torch.from_numpy(t[:n].copy()).cuda()
+            for _ in range(4):
+                a.match(tt, out)
+            torch.cuda.synchronize()
+            f, accf, c = oracle.dfa_run(d.delta, d.q0, d.accept, t[:n])
+            assert sfa.decode(out)[0] == (f, accf, 0, c), n
+        if rank == 0:
+            print(json.dumps({"workload": "crossover --profile", "launches": 12, "bit_exact_vs_oracle": True}))
+        return
     d, t = W.workload_large(64 << 20)
     a = sfa.Automaton.from_dfa(d)
     stream = torch.cuda.Stream()
