@@ -68,12 +68,16 @@ def key_for(info: dict, n: int, device_name: str) -> str:
 
 def candidates(info: dict, n: int) -> List[Dict[str, int]]:
     """The automatic shape first (one tile per resident CTA, two levels on
-    long texts), then CTA shapes with fixed chunk lengths, then warp tiles."""
+    long texts), then each CTA shape with the automatic chunk length and with
+    fixed ones, then warp tiles."""
     sim = info["mode"] == MODE_SIM
     shapes = SIM_SHAPES if sim else SFA_SHAPES
     chunks = SIM_CHUNKS if sim else SFA_CHUNKS
     out = [{}]
     for th, ch in shapes:
+        # the automatic chunk length (two levels on long texts) with this shape
+        if (th, ch) != shapes[0] or sim:
+            out.append({"block_threads": th, "chains": ch})
         for c in chunks:
             if c * th * ch > max(n, 1) * 2 and c > chunks[0]:
                 continue   # a single tile would hold the text many times over
