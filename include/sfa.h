@@ -297,6 +297,9 @@ int sfa_match_map(sfa_handle_t h, const uint8_t *d_text, uint64_t n, sfa_result 
  * Copies the text to the device in pieces on a second stream, overlapping
  * each copy with the matching of the previous piece (sfa_match_continue),
  * and synchronises before returning.  Uses handle-owned staging buffers.
+ * A text of up to 256 KiB in pinned host memory the device can read
+ * (mapped, e.g. from cudaHostAlloc) is matched in place, without a staging
+ * copy, when the automatic shape applies (no launch options set).
  */
 int sfa_match_host(sfa_handle_t h, const uint8_t *h_text, uint64_t n, sfa_result *h_out,
                    sfa_stream_t stream, const sfa_launch_opts *opts);

@@ -713,6 +713,28 @@ int sfa_match_host(sfa_handle_t h, const uint8_t *h_text, uint64_t n, sfa_result
         h->stage_bytes = piece;
     }
     int rc = SFA_OK;
+    // a short text in host memory the device can read (pinned and mapped):
+    // the short-text kernel reads it in place over the host link, so there
+    // is no staging copy and no event (up to IN_PLACE_MAX bytes: past that
+    // the staged copy, a copy-engine transfer, is faster than the kernel's
+    // reads of host memory); any other case is copied in pieces (the
+    // persistent kernel's bulk copies read device memory only)
+    constexpr uint64_t IN_PLACE_MAX = 256 << 10;
+    const bool shape_given = opts && (opts->chunk_bytes || opts->block_threads || opts->chains || opts->max_ctas ||
+                                      opts->forced_chunks || opts->debug_flags || opts->tiling);
+    if (n > 0 && n <= IN_PLACE_MAX && !shape_given && h->host.mode == SFA_MODE_SFA && !h->host.wide &&
+        h->host.nr <= 255 && small_fits(n)) {
+        if (const uint8_t *dp = device_readable(h_text)) {
+            rc = launch_small(h->dev, h->host.n_nc, dp, n, false, h->d_res, s);
+            if (rc == SFA_OK) {
+                CK(cudaMemcpyAsync(h_out, h->d_res, sizeof(sfa_result), cudaMemcpyDeviceToHost, s));
+                CK(cudaStreamSynchronize(s));
+                return SFA_OK;
+            }
+            if (rc != SFA_ERR_UNSUPPORTED) return rc;
+            rc = SFA_OK;
+        }
+    }
     if (n == 0) {
         rc = match_impl(h, nullptr, 0, h->d_res, s, opts, false);
         if (rc) return rc;

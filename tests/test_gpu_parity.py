@@ -732,6 +732,27 @@ def test_match_host_pinned_and_pageable():
     assert a.match_host(t[:0]) == expect(d, t[:0])
 
 
+@pytest.mark.parametrize("name", ["ac_set", "r5", "rand8", "one_state"])
+def test_match_host_short_pinned_in_place(name):
+    """Short pinned texts (up to 256 KiB) are read in place by the short-text
+    kernel (no staging copy): every length class up to and past 1 MiB, unaligned starts,
+    a pageable copy of each and an explicit shape (the copying path) agree
+    with the oracle; the next call on the same handle is unaffected."""
+    sfa = sfa_mod()
+    d = AUTOMATA[name]()
+    a = sfa.Automaton.from_dfa(d)
+    base = text_for(d, (1 << 20) + 64, seed=5)
+    pinned = torch.from_numpy(base).pin_memory()
+    for n in (1, 15, 1000, 16384, 16385, 65537, 300_001, 1 << 20, (1 << 20) + 1):
+        for off in (0, 3):
+            if off + n > base.size:
+                continue
+            want = expect(d, base[off:off + n])
+            assert a.match_host(pinned[off:off + n]) == want, (name, n, off)
+            assert a.match_host(base[off:off + n]) == want, (name, n, off)
+            assert a.match_host(pinned[off:off + n], block_threads=256, chains=1) == want, (name, n, off)
+
+
 def test_batch_mixed_and_graph():
     sfa = sfa_mod()
     autos_d = W.workload_batch_automata(4) + [W.dfa_rn(3), W.workload_sim_automata()[0]]
