@@ -185,10 +185,19 @@ def _check(code: int, what: str):
         raise SfaError(code, what)
 
 
+_NO_OPTS = None
+
+
 def _launch_opts(chunk_bytes=0, block_threads=0, chains=0, max_ctas=0, forced_chunks=0, timeout_us=0,
                  debug_flags=0, tiling=0) -> Optional[LaunchOpts]:
-    o = LaunchOpts(chunk_bytes, block_threads, chains, max_ctas, forced_chunks, timeout_us, debug_flags, tiling)
-    return o
+    global _NO_OPTS
+    if not (chunk_bytes or block_threads or chains or max_ctas or forced_chunks or timeout_us or debug_flags
+            or tiling):
+        # the automatic shape: one shared all-zero record (the library only reads it)
+        if _NO_OPTS is None:
+            _NO_OPTS = LaunchOpts(0, 0, 0, 0, 0, 0, 0, 0)
+        return _NO_OPTS
+    return LaunchOpts(chunk_bytes, block_threads, chains, max_ctas, forced_chunks, timeout_us, debug_flags, tiling)
 
 
 def _stream_ptr(stream) -> Optional[int]:
