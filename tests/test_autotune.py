@@ -15,6 +15,9 @@ def test_candidates_start_with_the_automatic_shape():
     c = autotune.candidates(info, 1 << 30)
     assert c[0] == {}
     assert {"block_threads": 512, "chains": 1, "tiling": 2} in c
+    # every other CTA shape also with the automatic chunk length (two levels)
+    assert {"block_threads": 1024, "chains": 1} in c and {"block_threads": 256, "chains": 2} in c
+    assert {"block_threads": 512, "chains": 1} not in c   # the automatic shape itself, listed first
     assert len({json.dumps(x, sort_keys=True) for x in c}) == len(c)
     sim = autotune.candidates({"mode": 2, "n_reachable": 16, "ncls": 16, "n_nonconst": 0}, 1 << 30)
     assert sim[0] == {} and all(x.get("block_threads", 128) in (128, 256) for x in sim)
