@@ -1,5 +1,5 @@
 // The short-text form of Alg. 5: one CTA matches a text of up to
-// SMALL_THREADS * SMALL_CHUNK bytes with no scratch memory, no bulk copies
+// SMALL_THREADS * SMALL_CHUNK bytes with no scratch memory, no tensor maps
 // and no look-back, for the latency of single short matches.  Each thread
 // loads its chunk into shared memory (word k of thread t at k * SMALL_THREADS
 // + t, so that a warp's reads of one word are conflict-free), runs the SFA
@@ -9,10 +9,11 @@
 // launch of a few microseconds lands on an SM whose instruction cache does
 // not hold this kernel, so its code is kept short.  The launch's latency is
 // a chain of dependent loads, so the tables arrive by asynchronous copies
-// issued together with the text's loads (one wait for all of them), the
-// non-constant rows are staged in shared memory when they fit (pass 1 then
-// never waits on L2), and the scans and the final sum use warp ballots and
-// shuffles instead of loops over shared memory.
+// issued together with the text's loads: the non-constant rows, staged in
+// shared memory when they fit (pass 1 then never waits on L2), by one bulk
+// copy on an mbarrier (a bounded wait), the other tables by cp.async; and
+// the scans and the final sum use warp ballots and shuffles instead of loops
+// over shared memory.
 //
 // Past one CTA's 64 KiB (and for latency already past 16 KiB) the same
 // kernel runs as a thread-block cluster of up to 16 CTAs, each matching a
