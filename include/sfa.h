@@ -299,7 +299,9 @@ int sfa_match_map(sfa_handle_t h, const uint8_t *d_text, uint64_t n, sfa_result 
  * and synchronises before returning.  Uses handle-owned staging buffers.
  * A text of up to 256 KiB in pinned host memory the device can read
  * (mapped, e.g. from cudaHostAlloc) is matched in place, without a staging
- * copy, when the automatic shape applies (no launch options set).
+ * copy, when the automatic shape applies (no launch options set); its result
+ * goes to a handle-owned mapped pinned record (allocated on the first such
+ * call) and is copied to h_out after the synchronisation.
  */
 int sfa_match_host(sfa_handle_t h, const uint8_t *h_text, uint64_t n, sfa_result *h_out,
                    sfa_stream_t stream, const sfa_launch_opts *opts);

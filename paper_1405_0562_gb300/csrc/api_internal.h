@@ -101,6 +101,8 @@ struct sfa_handle {
     uint8_t *d_stage[2] = {nullptr, nullptr};
     size_t stage_bytes = 0;
     sfa_result *d_res = nullptr;
+    sfa_result *h_res = nullptr;       // in-place matches: a mapped pinned result record
+    sfa_result *h_res_dev = nullptr;   // its device address
     cudaStream_t copy_stream = nullptr;
     cudaEvent_t ev_copied[2] = {nullptr, nullptr};
     cudaEvent_t ev_done[2] = {nullptr, nullptr};

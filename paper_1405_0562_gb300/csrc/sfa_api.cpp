@@ -547,6 +547,7 @@ void free_handle_device(sfa_handle *h) {
         if (h->ev_done[i]) cudaEventDestroy(h->ev_done[i]);
     }
     if (h->d_res) cudaFree(h->d_res);
+    if (h->h_res) cudaFreeHost(h->h_res);
     if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
 }
 
@@ -725,10 +726,15 @@ int sfa_match_host(sfa_handle_t h, const uint8_t *h_text, uint64_t n, sfa_result
     if (n > 0 && n <= IN_PLACE_MAX && !shape_given && h->host.mode == SFA_MODE_SFA && !h->host.wide &&
         h->host.nr <= 255 && small_fits(n)) {
         if (const uint8_t *dp = device_readable(h_text)) {
-            rc = launch_small(h->dev, h->host.n_nc, dp, n, false, h->d_res, s);
+            // the kernel writes its result straight to mapped pinned memory
+            if (!h->h_res) {
+                CK(cudaHostAlloc(reinterpret_cast<void **>(&h->h_res), sizeof(sfa_result), cudaHostAllocMapped));
+                CK(cudaHostGetDevicePointer(reinterpret_cast<void **>(&h->h_res_dev), h->h_res, 0));
+            }
+            rc = launch_small(h->dev, h->host.n_nc, dp, n, false, h->h_res_dev, s);
             if (rc == SFA_OK) {
-                CK(cudaMemcpyAsync(h_out, h->d_res, sizeof(sfa_result), cudaMemcpyDeviceToHost, s));
                 CK(cudaStreamSynchronize(s));
+                std::memcpy(h_out, h->h_res, sizeof(sfa_result));
                 return SFA_OK;
             }
             if (rc != SFA_ERR_UNSUPPORTED) return rc;
