@@ -229,7 +229,7 @@ const char *sfa_strerror(int code);
 
 typedef struct {
     uint32_t chunk_bytes;     /* bytes per chunk (any value >= 1; 0 = automatic) */
-    uint32_t block_threads;   /* 128, 256 or 512 (0 = automatic) */
+    uint32_t block_threads;   /* 128, 256, 512, or 1024 with chains = 1 (0 = automatic) */
     uint32_t chains;          /* chunks per thread: 1, 2 or 4 (0 = automatic) */
     uint32_t max_ctas;        /* cap on resident CTAs (0 = all that fit) */
     uint32_t forced_chunks;   /* >0: split the text into exactly this many chunks of
@@ -250,6 +250,11 @@ typedef struct {
  * mappings are combined by warp, block and grid (decoupled look-back) scans
  * of reverse compositions (Lemma 1, Theorem 3); a second pass over each
  * chunk's prefix before its last "mixed" position counts final states.
+ * With no launch options, a D-SFA handle with byte state ids matches a text
+ * of up to 1 MiB with the short-text kernel instead: one CTA (up to 16 KiB)
+ * or a thread-block cluster of up to 16 CTAs whose aggregates meet in
+ * distributed shared memory; no scratch and no look-back (a cluster size the
+ * device cannot hold resident falls back to the persistent kernel).
  * May grow the handle's scratch (cudaMalloc) when n exceeds all previous calls.
  */
 int sfa_match(sfa_handle_t h, const uint8_t *d_text, uint64_t n, sfa_result *d_out,
